@@ -1,0 +1,88 @@
+"""Checks that the oracle's pins are sharp: each plausible mistake below (a
+dropped term, a wrong sign, index or offset, a swapped operand) is planted in a
+copy of the oracle's C source on the CPU, built, and the pin suite must fail
+against that build.  Nothing here touches a GPU."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pic_oracle.c")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+MUTATIONS = [
+    ("boris: gamma dropped from t", "t[a] = k * eb[3 + a] / gm;", "t[a] = k * eb[3 + a];"),
+    ("boris: u- x t sign", "ud[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);",
+     "ud[0] = um[0] + (um[2] * t[1] - um[1] * t[2]);"),
+    ("boris: s without factor 2", "sv[a] = 2.0 * t[a] / (1.0 + t2);", "sv[a] = t[a] / (1.0 + t2);"),
+    ("boris: second half kick dropped", "u[a] = up[a] + k * eb[a];", "u[a] = up[a];"),
+    ("push: non-relativistic position update", "np_[a] = pos[a] + s->dt * u[a] / g;",
+     "np_[a] = pos[a] + s->dt * u[a];"),
+    ("staggering: Bx at a cell centre", "{0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}", "{0.5, 0.5, 0.5}, {0.5, 0.0, 0.5}"),
+    ("staggering: Ez at a node", "{0.0, 0.0, 0.5}, /* E */", "{0.0, 0.0, 0.0}, /* E */"),
+    ("esirkepov: 1/3 term as 1/2", "0.5 * S0[1][m] * DS[2][n] + DS[1][m] * DS[2][n] / 3.0);",
+     "0.5 * S0[1][m] * DS[2][n] + DS[1][m] * DS[2][n] / 2.0);"),
+    ("esirkepov: half term without 1/2", "double W = DS[0][l] * (S0[1][m] * S0[2][n] + 0.5 * DS[1][m] * S0[2][n] +",
+     "double W = DS[0][l] * (S0[1][m] * S0[2][n] + DS[1][m] * S0[2][n] +"),
+    ("esirkepov: current sign", "const double cx = -qw / (dy * dz * dt);", "const double cx = qw / (dy * dz * dt);"),
+    ("esirkepov 2D: out-of-plane 1/3 term", "DSx[l] * DSz[n] / 3.0;", "DSx[l] * DSz[n] / 2.0;"),
+    ("esirkepov 2D: Jz weight", "acc += DSz[n] * (S0x[l] + 0.5 * DSx[l]);", "acc += DSz[n] * (S0x[l] + DSx[l]);"),
+    ("esirkepov: quadratic window from floor(x)", "return (int64_t)floor(X0 + 0.5) - 2;",
+     "return (int64_t)floor(X0) - 2;"),
+    ("ampere: J sign", "F(ORC_EX, i, j, k) += dt * (cBx - F(ORC_JX, i, j, k));",
+     "F(ORC_EX, i, j, k) += dt * (cBx + F(ORC_JX, i, j, k));"),
+    ("faraday: backward instead of forward difference",
+     "double cEx = (F(ORC_EZ, i, j + 1, k) - F(ORC_EZ, i, j, k)) * iy -",
+     "double cEx = (F(ORC_EZ, i, j, k) - F(ORC_EZ, i, j - 1, k)) * iy -"),
+    ("ampere: forward instead of backward difference",
+     "double cBz = (F(ORC_BY, i, j, k) - F(ORC_BY, i - 1, j, k)) * ix -",
+     "double cBz = (F(ORC_BY, i + 1, j, k) - F(ORC_BY, i, j, k)) * ix -"),
+    ("faraday: full instead of half step", "const double h = 0.5 * s->dt;", "const double h = s->dt;"),
+    ("shape: quadratic centre value", "if (a < 0.5) return 0.75 - a * a;", "if (a < 0.5) return 0.75 - 0.5 * a * a;"),
+    ("gather: linear support from the nearest node", "if (order == 1) return (int64_t)floor(xi);",
+     "if (order == 1) return (int64_t)floor(xi + 0.5);"),
+    ("knapsack: ties to the highest worker", "if (best < 0 || load[w] < load[best]) best = w;",
+     "if (best < 0 || load[w] <= load[best]) best = w;"),
+    ("knapsack: ascending instead of descending", "while (j >= 0 && costs[order[j]] < costs[v])",
+     "while (j >= 0 && costs[order[j]] > costs[v])"),
+    ("morton: y and z bits swapped", "key |= (uint64_t)((by >> i) & 1) << (3 * i + 1);",
+     "key |= (uint64_t)((by >> i) & 1) << (3 * i + 2);"),
+    ("sfc: strict threshold off by one worker", "if (prefix * (double)n_workers >= (double)(w + 1) * total && w < n_workers - 1) w++;",
+     "if (prefix * (double)n_workers >= (double)(w) * total && w < n_workers - 1) w++;"),
+    ("efficiency: total instead of average", "return (total / (double)n_workers) / mx;", "return total / mx;"),
+    ("threshold: strict improvement", "return e_new >= (1.0 + theta) * e_old;", "return e_new > (1.0 + theta) * e_old;"),
+    ("antenna: sheet amplitude without factor 2", "double amp = 2.0 * s->las_a0 / s->d[2] * env;",
+     "double amp = s->las_a0 / s->d[2] * env;"),
+    ("damping layer disabled", "if (s->absorb <= 0) return;\n    for (int64_t k = 0;", "return;\n    for (int64_t k = 0;"),
+    ("particles: upper absorbing boundary ignored", "if (np_[2] < zlo || np_[2] >= zhi) drop[ndrop++] = p;",
+     "if (np_[2] < zlo) drop[ndrop++] = p;"),
+    ("speedup model: exponent dropped", "return pow(1.0 / e0, x);", "return 1.0 / e0;"),
+]
+
+
+def _run_mutant(idx, desc, old, new, tmpdir):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique or missing: {desc}"
+    mpath = os.path.join(tmpdir, f"m{idx}.c")
+    lpath = os.path.join(tmpdir, f"libm{idx}.so")
+    with open(mpath, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", lpath, mpath, "-lm"])
+    env = dict(os.environ, PIC_ORACLE_LIB=lpath)
+    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return desc, r.returncode
+
+
+def test_every_planted_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+            futs = [ex.submit(_run_mutant, i, *m, tmp) for i, m in enumerate(MUTATIONS)]
+            results = [f.result() for f in futs]
+    survivors = [d for d, rc in results if rc == 0]
+    assert not survivors, f"pins did not catch: {survivors}"

@@ -1,0 +1,509 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each expected value comes from a
+closed form (discrete dispersion, exact Boris rotation, leapfrog plasma
+frequency), a conservation law (Esirkepov continuity, Gauss), a textbook
+property (B-spline partition of unity, exact interpolation of linear fields), a
+brute-force search on tiny inputs, or a number the paper prints.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- shapes ---
+def test_shape_values_and_partition_of_unity():
+    # textbook B-spline values
+    assert orc.shape(1, 0.0) == 1.0 and orc.shape(1, 0.25) == 0.75 and orc.shape(1, 1.0) == 0.0
+    assert orc.shape(2, 0.0) == 0.75 and orc.shape(2, 0.5) == 0.5
+    assert orc.shape(2, 1.0) == 0.125 and orc.shape(2, 1.5) == 0.0
+    rng = np.random.default_rng(0)
+    for order in (1, 2):
+        for x in rng.uniform(-3, 3, 50):
+            nodes = np.arange(math.floor(x) - 3, math.floor(x) + 4)
+            vals = [orc.shape(order, x - k) for k in nodes]
+            assert abs(sum(vals) - 1.0) < 1e-15
+            # first moment: shape centred on the particle
+            assert abs(sum(v * k for v, k in zip(vals, nodes)) - x) < 1e-13
+
+
+# ---------------------------------------------------------------- gather ---
+STAG = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+
+
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 1), (2, 2)])
+def test_gather_reproduces_linear_fields(dim, order):
+    """Linear and quadratic B-splines interpolate affine fields exactly, so any
+    error in a component's staggering offset shows up as a b*dx/2 bias."""
+    n = (12, 12 if dim == 3 else 1, 12)
+    d = (0.3, 0.4 if dim == 3 else 1.0, 0.5)
+    sim = orc.OracleSim(dim, n, d, 0.1, order)
+    rng = np.random.default_rng(1)
+    coef = rng.normal(size=(6, 4))
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    for c in range(6):
+        sx, sy, sz = STAG[c]
+        X = (i + sx) * d[0]
+        Y = (j + sy) * d[1] if dim == 3 else 0 * X
+        Z = (k + sz) * d[2]
+        sim.set_field(c, coef[c, 0] + coef[c, 1] * X + coef[c, 2] * Y + coef[c, 3] * Z)
+    for _ in range(40):
+        x = rng.uniform(3, 8) * d[0]
+        y = rng.uniform(3, 8) * d[1] if dim == 3 else 0.0
+        z = rng.uniform(3, 8) * d[2]
+        got = sim.gather(x, y, z)
+        want = coef[:, 0] + coef[:, 1] * x + coef[:, 2] * y + coef[:, 3] * z
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- Boris ---
+@pytest.mark.parametrize("q", [1.0, -1.0])
+def test_boris_exact_gyration(q):
+    """E = 0, uniform B along z: every push rotates u about z by exactly
+    2*atan(q B dt / (2 m gamma)) (clockwise for q > 0), |u| is conserved."""
+    B0, dt, m = 1.7, 0.3, 1.0
+    u = np.array([0.8, 0.0, 0.3])
+    g = math.sqrt(1 + u @ u)
+    theta = 2 * math.atan(q * B0 * dt / (2 * m * g))
+    eb = np.array([0, 0, 0, 0, 0, B0])
+    uu = u.copy()
+    for n in range(1, 1001):
+        uu = orc.boris(q, m, dt, eb, uu)
+        assert abs(math.sqrt(uu @ uu) - math.sqrt(u @ u)) < 1e-14
+    ang = -1000 * theta
+    want = np.array([u[0] * math.cos(ang), u[0] * math.sin(ang), u[2]])
+    np.testing.assert_allclose(uu, want, atol=2e-12)
+
+
+def test_boris_pure_electric_kick():
+    """B = 0: the two half kicks add to q E dt / m exactly."""
+    E = np.array([0.3, -0.2, 0.5])
+    eb = np.concatenate([E, np.zeros(3)])
+    u = np.array([0.1, 0.2, -0.3])
+    out = orc.boris(-1.0, 2.0, 0.25, eb, u)
+    np.testing.assert_allclose(out, u + (-1.0) * E * 0.25 / 2.0, rtol=0, atol=1e-15)
+
+
+def test_gyration_orbit_in_full_cycle():
+    """A single test particle (negligible weight) in a uniform Bz: the
+    position after N cycles is the closed-form sum of the rotated velocities."""
+    n, d, dt = (8, 8, 8), (0.5, 0.5, 0.5), 0.2
+    sim = orc.OracleSim(3, n, d, dt, 1)
+    B0 = 0.9
+    sim.set_field(orc.BZ, np.full(512, B0))
+    u0 = np.array([0.4, 0.1, 0.05])
+    x0 = np.array([2.0, 2.0, 2.0])
+    q = -1.0
+    sim.add_species(q, 1.0, [x0[0]], [x0[1]], [x0[2]], [u0[0]], [u0[1]], [u0[2]], [1e-300])
+    N = 37
+    sim.step(N)
+    g = math.sqrt(1 + u0 @ u0)
+    phi = -2 * math.atan(q * B0 * dt / (2 * g))  # rotation angle per step (counter-clockwise)
+    zeta = complex(math.cos(phi), math.sin(phi))
+    w0 = complex(u0[0], u0[1])
+    s = w0 * zeta * (1 - zeta ** N) / (1 - zeta)  # sum_{m=1..N} zeta^m w0
+    L = 4.0
+    want = np.array([(x0[0] + dt * s.real / g) % L, (x0[1] + dt * s.imag / g) % L,
+                     (x0[2] + N * dt * u0[2] / g) % L])
+    p = sim.particles(0)
+    np.testing.assert_allclose([p["x"][0], p["y"][0], p["z"][0]], want, atol=1e-12)
+    uz = u0[2]
+    wN = w0 * zeta ** N
+    np.testing.assert_allclose([p["ux"][0], p["uy"][0], p["uz"][0]], [wN.real, wN.imag, uz],
+                               atol=1e-13)
+
+
+def test_uniform_E_acceleration_relativistic():
+    n, d, dt = (4, 4, 4), (0.5, 0.5, 0.5), 0.1
+    sim = orc.OracleSim(3, n, d, dt, 2)
+    E0 = 0.7
+    sim.set_field(orc.EX, np.full(64, E0))
+    q, m = 1.0, 3.0
+    sim.add_species(q, m, [1.0], [1.0], [1.0], [0.0], [0.0], [0.0], [1e-300])
+    N = 25
+    sim.step(N)
+    p = sim.particles(0)
+    # u^{n+1/2} = n q E dt / m ; x^{n+1} = x^n + dt u / gamma
+    us = [(k + 1) * q * E0 * dt / m for k in range(N)]
+    x = 1.0 + sum(dt * u / math.sqrt(1 + u * u) for u in us)
+    assert abs(p["ux"][0] - us[-1]) < 1e-14
+    assert abs(p["x"][0] - (x % 2.0)) < 1e-13
+
+
+# ------------------------------------------------------------------- Yee ---
+def _yee_mode(dim, n, d, dt, kvec_int, a_vec):
+    L = np.array([n[0] * d[0], n[1] * d[1], n[2] * d[2]])
+    k = 2 * np.pi * np.array(kvec_int) / L
+    kap = 2 * np.sin(k * np.array(d) / 2) / np.array(d)
+    if dim == 2:
+        kap[1] = 0.0
+        k[1] = 0.0
+    Om = np.linalg.norm(kap)
+    w = 2 / dt * math.asin(dt * Om / 2)
+    Ehat = np.cross(kap, a_vec)
+    Ehat /= np.linalg.norm(Ehat)
+    Bhat = np.cross(kap, Ehat) / Om
+    return k, w, Ehat, Bhat
+
+
+def _yee_fields(dim, n, d, k, w, Ehat, Bhat, dt, step):
+    kk, jj, ii = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    out = []
+    for c in range(6):
+        sx, sy, sz = STAG[c]
+        ph = k[0] * (ii + sx) * d[0] + k[2] * (kk + sz) * d[2] - w * step * dt
+        if dim == 3:
+            ph = ph + k[1] * (jj + sy) * d[1]
+        if c < 3:
+            out.append(Ehat[c] * np.cos(ph))
+        else:
+            out.append(Bhat[c - 3] * math.cos(w * dt / 2) * np.cos(ph))
+    return out
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_yee_vacuum_dispersion(dim):
+    """Yee eigenmode: after N steps the fields equal the travelling wave whose
+    frequency obeys (sin(w dt/2)/dt)^2 = sum_i (sin(k_i dx_i/2)/dx_i)^2."""
+    if dim == 3:
+        n, d, kint, a = (12, 10, 8), (0.3, 0.35, 0.4), (1, 2, 3), np.array([0.0, 0.0, 1.0])
+    else:
+        n, d, kint, a = (16, 1, 12), (0.3, 1.0, 0.4), (1, 0, 2), np.array([0.0, 1.0, 0.0])
+    dt = 0.9 / math.sqrt(sum(1 / v ** 2 for v, ax in zip(d, range(3)) if not (dim == 2 and ax == 1)))
+    k, w, Eh, Bh = _yee_mode(dim, n, d, dt, kint, a)
+    sim = orc.OracleSim(dim, n, d, dt, 1)
+    for c, f in enumerate(_yee_fields(dim, n, d, k, w, Eh, Bh, dt, 0)):
+        sim.set_field(c, f)
+    N = 60
+    sim.step(N)
+    want = _yee_fields(dim, n, d, k, w, Eh, Bh, dt, N)
+    for c in range(6):
+        np.testing.assert_allclose(sim.field(c), want[c], rtol=0, atol=1e-12)
+    # div B stays zero
+    Bx, By, Bz = (sim.field(c) for c in (3, 4, 5))
+    divB = (np.roll(Bx, -1, 2) - Bx) / d[0] + (np.roll(Bz, -1, 0) - Bz) / d[2]
+    if dim == 3:
+        divB += (np.roll(By, -1, 1) - By) / d[1]
+    assert np.abs(divB).max() < 1e-12
+
+
+# ------------------------------------------------------- plasma frequency ---
+@pytest.mark.parametrize("order", [1, 2])
+def test_cold_plasma_oscillation_leapfrog_frequency(order):
+    """Uniform cold electrons (lattice loaded) drifting with u0 over fixed
+    ions: the k = 0 mode is the leapfrog oscillator with
+    sin(w dt / 2) = w_pe dt / 2, so u^{n+1/2} = u0 cos(w (n+1/2) dt) / cos(w dt/2)."""
+    n, d, dt = (4, 4, 4), (0.5, 0.5, 0.5), 0.15
+    ppc_side = 2
+    n0 = 1.0  # w_pe^2 = n0 q^2 / m = 1
+    offs = (np.arange(ppc_side) + 0.5) / ppc_side
+    pts = []
+    for k, j, i in itertools.product(range(n[2]), range(n[1]), range(n[0])):
+        for oz, oy, ox in itertools.product(offs, offs, offs):
+            pts.append(((i + ox) * d[0], (j + oy) * d[1], (k + oz) * d[2]))
+    pts = np.array(pts)
+    npart = len(pts)
+    w = n0 * d[0] * d[1] * d[2] / ppc_side ** 3
+    u0 = 1e-6
+    sim = orc.OracleSim(3, n, d, dt, order)
+    sim.add_species(-1.0, 1.0, pts[:, 0], pts[:, 1], pts[:, 2], np.full(npart, u0),
+                    np.zeros(npart), np.zeros(npart), np.full(npart, w))
+    wfreq = 2 / dt * math.asin(dt * math.sqrt(n0) / 2)
+    for step in range(1, 60):
+        sim.step(1)
+        ux = sim.particles(0)["ux"]
+        want = u0 * math.cos(wfreq * (step - 0.5) * dt) / math.cos(wfreq * dt / 2)
+        assert np.abs(ux - want).max() < 1e-9 * u0
+
+
+# ------------------------------------------------------ charge continuity ---
+def _random_plasma(dim, n, d, rng, npart, umax):
+    L = [n[a] * d[a] for a in range(3)]
+    x = rng.uniform(0, L[0], npart)
+    y = rng.uniform(0, L[1], npart) if dim == 3 else np.zeros(npart)
+    z = rng.uniform(0, L[2], npart)
+    u = rng.normal(size=(3, npart))
+    u *= umax / np.maximum(np.linalg.norm(u, axis=0), 1e-300) * rng.uniform(0, 1, npart)
+    w = rng.uniform(0.5, 1.5, npart)
+    return x, y, z, u[0], u[1], u[2], w
+
+
+def _div_nodes(dim, n, d, Fx, Fy, Fz):
+    div = (Fx - np.roll(Fx, 1, 2)) / d[0] + (Fz - np.roll(Fz, 1, 0)) / d[2]
+    if dim == 3:
+        div += (Fy - np.roll(Fy, 1, 1)) / d[1]
+    return div
+
+
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 1), (2, 2)])
+def test_esirkepov_discrete_continuity(dim, order):
+    """(rho^{n+1} - rho^n)/dt + div J^{n+1/2} = 0 at every node (Esirkepov
+    2001), with rho deposited by S at the nodes; fast particles so that many
+    cross cell boundaries."""
+    n = (6, 5 if dim == 3 else 1, 7)
+    d = (0.4, 0.5 if dim == 3 else 1.0, 0.45)
+    inv = sum(1 / d[a] ** 2 for a in range(3) if not (dim == 2 and a == 1))
+    dt = 0.99 / math.sqrt(inv)
+    rng = np.random.default_rng(10 + dim + order)
+    sim = orc.OracleSim(dim, n, d, dt, order)
+    parts = _random_plasma(dim, n, d, rng, 300, umax=3.0)
+    sim.add_species(-1.0, 1.0, *parts)
+    sim.add_species(2.0, 5.0, *_random_plasma(dim, n, d, rng, 200, umax=1.0))
+    # random smooth fields to get varied pushes
+    for c in range(6):
+        sim.set_field(c, 0.3 * rng.normal(size=sim.ncell))
+    rho0 = sim.rho()
+    sim.step(1)
+    rho1 = sim.rho()
+    J = [sim.field(c) for c in (orc.JX, orc.JY, orc.JZ)]
+    res = (rho1 - rho0) / dt + _div_nodes(dim, n, d, *J)
+    scale = np.abs(rho0).max() / dt
+    assert np.abs(res).max() < 1e-13 * scale
+    assert np.abs(J[0]).max() > 1e-3 * scale * d[0]  # currents are not trivially zero
+
+
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 2)])
+def test_gauss_law_residual_preserved(dim, order):
+    """Charge-conserving deposit + Yee: div E - rho changes by roundoff only."""
+    n = (6, 6 if dim == 3 else 1, 6)
+    d = (0.5, 0.5 if dim == 3 else 1.0, 0.5)
+    inv = sum(1 / d[a] ** 2 for a in range(3) if not (dim == 2 and a == 1))
+    dt = 0.95 / math.sqrt(inv)
+    rng = np.random.default_rng(20 + dim + order)
+    sim = orc.OracleSim(dim, n, d, dt, order)
+    sim.add_species(-1.0, 1.0, *_random_plasma(dim, n, d, rng, 400, umax=0.8))
+    sim.add_species(1.0, 1836.15267343, *_random_plasma(dim, n, d, rng, 400, umax=0.01))
+
+    def residual():
+        E = [sim.field(c) for c in (orc.EX, orc.EY, orc.EZ)]
+        return _div_nodes(dim, n, d, *E) - sim.rho()
+
+    r0 = residual()
+    scale = np.abs(sim.rho()).max()
+    for _ in range(8):
+        sim.step(1)
+        assert np.abs(residual() - r0).max() < 1e-13 * scale
+
+
+# --------------------------------------------------------------- antenna ---
+def test_antenna_radiates_amplitude_a0():
+    """A sheet current Jx = 2 a0 / dz radiates a plane wave of amplitude a0
+    (|E| = |K| / 2 for a current sheet K with c = mu0 = 1)."""
+    n, d = (4, 1, 256), (0.2, 1.0, 0.2)
+    dt = 0.98 * d[2]
+    sim = orc.OracleSim(2, n, d, dt, 1, absorb_cells=40)
+    a0 = 0.5
+    sim.set_laser(a0, 1e9, 1e9, 0.0, 1.0, 0.0, 0.0, 60)
+    sim.step(300)
+    ex = sim.field(orc.EX)[:, 0, 0]
+    # forward wave region ahead of the antenna, away from the absorbing layer
+    seg = ex[90:200]
+    assert 0.97 * a0 < np.abs(seg).max() < 1.03 * a0
+
+
+def test_damping_layer_absorbs_outgoing_pulse():
+    n, d = (4, 1, 200), (0.2, 1.0, 0.2)
+    dt = 0.98 * d[2]
+    sim = orc.OracleSim(2, n, d, dt, 1, absorb_cells=40)
+    sim.set_laser(1.0, 1e9, 2.0, 6.0, 1.0, 0.0, 0.0, 100)
+    sim.step(90)
+    e_mid = sum(float((sim.field(c) ** 2).sum()) for c in range(6))
+    sim.step(260)
+    e_end = sum(float((sim.field(c) ** 2).sum()) for c in range(6))
+    assert e_mid > 0 and e_end < 0.05 * e_mid
+
+
+def test_absorbed_particles_are_removed_by_id():
+    n, d, dt = (4, 4, 16), (0.5, 0.5, 0.5), 0.2
+    sim = orc.OracleSim(3, n, d, dt, 1, absorb_cells=2)
+    # z layer boundaries at 1.0 and 7.0
+    sim.add_species(-1.0, 1.0, [1.0, 1.0, 1.0], [1.0, 1.0, 1.0], [1.02, 4.0, 6.98],
+                    [0, 0, 0], [0, 0, 0], [-0.5, 0.0, 0.5], [1e-300] * 3, ids=[7, 8, 9])
+    sim.step(1)
+    p = sim.particles(0)
+    assert list(p["id"]) == [8]
+
+
+# -------------------------------------------------------- load balancing ---
+def test_fig1_efficiency_from_paper():
+    g = json.load(open(os.path.join(HERE, "golden", "fig1_lb_example.json")))
+    costs = np.array(g["particle_counts"], dtype=float)
+    E = orc.lb_efficiency(costs, g["mapping_b"], g["n_ranks"])
+    assert E == g["efficiency_mapping_b_particle_cost"]
+    # a knapsack mapping of the same costs puts the two loaded boxes on
+    # different ranks: E = 15 / 18
+    a = orc.knapsack(costs, 2)
+    assert a[0] != a[3]
+    assert orc.lb_efficiency(costs, a, 2) == pytest.approx(15 / 18, abs=1e-15)
+    s = orc.sfc(costs, g["box_ijk"], 2, 2)
+    assert orc.lb_efficiency(costs, s, 2) >= 0.5
+
+
+def test_efficiency_edge_cases():
+    assert orc.lb_efficiency([0, 0, 0], [0, 1, 1], 2) == 1.0
+    assert orc.lb_efficiency([1, 1, 1, 1], [0, 1, 0, 1], 2) == 1.0
+    assert orc.lb_efficiency([4, 0], [0, 0], 4) == 0.25
+
+
+def _brute_opt(costs, m):
+    best = float("inf")
+    for assign in itertools.product(range(m), repeat=len(costs)):
+        loads = [0.0] * m
+        for c, a in zip(costs, assign):
+            loads[a] += c
+        best = min(best, max(loads))
+    return best
+
+
+def test_knapsack_graham_bound_against_brute_force():
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        nb = int(rng.integers(1, 9))
+        m = int(rng.integers(1, 4))
+        costs = rng.integers(0, 20, nb).astype(float)
+        a = orc.knapsack(costs, m, cap_factor=1e9)  # uncapped: plain LPT
+        loads = np.bincount(a, weights=costs, minlength=m)
+        opt = _brute_opt(costs, m)
+        assert loads.max() >= opt - 1e-12
+        assert loads.max() <= (4 / 3 - 1 / (3 * m)) * opt + 1e-12
+
+
+def test_knapsack_tie_rules_and_cap():
+    # equal costs: lower box index first, lowest worker id wins ties
+    a = orc.knapsack([1.0, 1.0, 1.0, 1.0], 2)
+    assert list(a) == [0, 1, 0, 1]
+    # cap: 6 boxes, 3 workers, cap = max(ceil(2), floor(1.5*2)) = 3 boxes per worker
+    costs = [100.0, 1.0, 1.0, 1.0, 1.0, 1.0]
+    a = orc.knapsack(costs, 3)
+    cnt = np.bincount(a, minlength=3)
+    assert cnt.max() <= 3 and a[0] == 0
+    # with cap_factor 1.0 the cap is 2 boxes per worker
+    a = orc.knapsack(costs, 3, cap_factor=1.0)
+    assert np.bincount(a, minlength=3).max() <= 2
+
+
+def test_morton_keys_by_hand():
+    assert orc.morton(3, 1, 0, 0) == 1
+    assert orc.morton(3, 0, 1, 0) == 2
+    assert orc.morton(3, 0, 0, 1) == 4
+    assert orc.morton(3, 1, 1, 1) == 7
+    assert orc.morton(3, 2, 0, 0) == 8
+    assert orc.morton(3, 3, 5, 6) == 427
+    assert orc.morton(2, 1, 0, 0) == 1
+    assert orc.morton(2, 0, 0, 1) == 2
+    assert orc.morton(2, 3, 0, 1) == 7
+    # 4x4 2D grid: the Z curve visits (0,0) (1,0) (0,1) (1,1) (2,0) ...
+    order = sorted(((x, z) for x in range(4) for z in range(4)), key=lambda p: orc.morton(2, p[0], 0, p[1]))
+    assert order[:8] == [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (3, 0), (2, 1), (3, 1)]
+
+
+def _contiguous_opt(costs, m):
+    """min over contiguous partitions of the sequence into m pieces of the max piece sum (DP)."""
+    nb = len(costs)
+    pre = np.concatenate([[0.0], np.cumsum(costs)])
+    INF = float("inf")
+    f = [[INF] * (nb + 1) for _ in range(m + 1)]
+    f[0][0] = 0.0
+    for k in range(1, m + 1):
+        for i in range(nb + 1):
+            for j in range(i + 1):
+                f[k][i] = min(f[k][i], max(f[k - 1][j], pre[i] - pre[j]))
+    return f[m][nb]
+
+
+def test_sfc_contiguous_and_bounded():
+    rng = np.random.default_rng(6)
+    ijk = np.array([(x, y, z) for z in range(2) for y in range(2) for x in range(4)], dtype=np.int32)
+    for trial in range(30):
+        costs = rng.lognormal(0, 1.5, len(ijk))
+        m = int(rng.integers(1, 6))
+        a = orc.sfc(costs, ijk, 3, m)
+        keys = [orc.morton(3, *p) for p in ijk]
+        seq = np.argsort(keys)
+        # worker ids are non-decreasing along the curve (contiguous pieces)
+        assert np.all(np.diff(a[seq]) >= 0)
+        loads = np.bincount(a, weights=costs, minlength=m)
+        opt = _contiguous_opt(list(costs[seq]), m)
+        assert loads.max() >= opt - 1e-12
+        assert loads.max() <= costs.sum() / m + costs.max() + 1e-12
+
+
+def test_threshold_meets_or_exceeds():
+    assert orc.lb_adopt(0.5, 0.625, 0.25)
+    assert not orc.lb_adopt(0.5, 0.62499999, 0.25)
+    assert orc.lb_adopt(0.5, 0.5, 0.0)
+
+
+def test_performance_model_paper_values():
+    """Sec. 4: c_max0/c_avg0 = 6.2 with x = 0.91 (2D3V) or 0.88 (3D3V) gives a
+    best speedup of about 5x."""
+    for x in (0.91, 0.88):
+        s = orc.predicted_speedup(1 / 6.2, x)
+        assert round(s) == 5
+    assert orc.predicted_speedup(1.0, 0.9) == 1.0
+
+
+# ------------------------------------------- in-cell line-integral current ---
+def _gl3(f):
+    """3-point Gauss-Legendre on [0, 1]: exact for polynomials of degree <= 5."""
+    xs = [0.5 - 0.5 * math.sqrt(0.6), 0.5, 0.5 + 0.5 * math.sqrt(0.6)]
+    ws = [5 / 18, 8 / 18, 5 / 18]
+    return sum(w * f(x) for w, x in zip(ws, xs))
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_linear_deposit_equals_line_integral_for_in_cell_motion(dim):
+    """With linear shapes and a straight move that stays inside one cell, the
+    charge-conserving current through each cell face is the exact time
+    integral of q v S(y(t)) S(z(t)) along the path (Villasenor-Buneman); this
+    pins every Esirkepov weight term, including the 2D out-of-plane Jy."""
+    n = (6, 6 if dim == 3 else 1, 6)
+    d = (0.5, 0.5 if dim == 3 else 1.0, 0.5)
+    dt = 0.1
+    rng = np.random.default_rng(40 + dim)
+    for trial in range(10):
+        sim = orc.OracleSim(dim, n, d, dt, 1)
+        X0 = np.array([2.0, 2.0 if dim == 3 else 0.0, 3.0]) + rng.uniform(0.2, 0.8, 3)
+        if dim == 2:
+            X0[1] = 0.0
+        u = rng.uniform(-0.5, 0.5, 3)
+        g = math.sqrt(1 + u @ u)
+        v = u / g
+        dX = v * dt / np.array(d)
+        if dim == 2:
+            dX[1] = 0.0
+        q, w = -1.0, 0.7
+        pos = X0 * np.array(d)
+        sim.add_species(q, 1.0, [pos[0]], [pos[1]], [pos[2]], [u[0]], [u[1]], [u[2]], [w])
+        sim.step(1)  # zero fields: the push leaves u unchanged
+        J = [sim.field(c) for c in (orc.JX, orc.JY, orc.JZ)]
+        V = d[0] * d[1] * d[2]
+        i0 = np.floor(X0).astype(int)
+
+        def hat(t, a, node):
+            return max(0.0, 1 - abs(X0[a] + t * dX[a] - node))
+
+        want = [np.zeros_like(J[0]) for _ in range(3)]
+        ys = [i0[1], i0[1] + 1] if dim == 3 else [0]
+        for kk in (i0[2], i0[2] + 1):
+            for jj in ys:
+                for ii in (i0[0], i0[0] + 1):
+                    hy = (lambda t, jj=jj: hat(t, 1, jj)) if dim == 3 else (lambda t: 1.0)
+                    if ii == i0[0]:
+                        want[0][kk, jj, ii] = q * w * v[0] / V * _gl3(lambda t: hy(t) * hat(t, 2, kk))
+                    if kk == i0[2]:
+                        want[2][kk, jj, ii] = q * w * v[2] / V * _gl3(lambda t: hat(t, 0, ii) * hy(t))
+                    if dim == 3 and jj == i0[1]:
+                        want[1][kk, jj, ii] = q * w * v[1] / V * _gl3(lambda t: hat(t, 0, ii) * hat(t, 2, kk))
+                    if dim == 2:
+                        want[1][kk, jj, ii] = q * w * v[1] / V * _gl3(lambda t: hat(t, 0, ii) * hat(t, 2, kk))
+        for c in range(3):
+            np.testing.assert_allclose(J[c], want[c], rtol=0, atol=1e-14)

@@ -1,0 +1,272 @@
+// pic_fields.cu -- the cell side of the PIC cycle: Yee FDTD update (the
+// finite-difference time-domain field solve named in arXiv 2104.11385 Sec. 3.3)
+// as B half step, E full step with the deposited current (and the laser
+// antenna source of Sec. 3.1), B half step; z damping layers; periodic guard
+// fill of the padded E/B arrays for the next step's TMA tile loads.
+//
+// Each cell update reads E,B,J and writes E,B: HBM-bound elementwise work, one
+// thread per cell, x fastest for coalescing.
+#include "pic_internal.h"
+
+namespace {
+
+__device__ __forceinline__ int nxt(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+__device__ __forceinline__ int prv(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+
+template <int DIM>
+__global__ void b_half_kernel(const SimDev* __restrict__ sims) {
+    const SimDev& S = sims[0];
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    const double h = 0.5 * S.dt;
+    const double ix = 1.0 / S.d[0], iy = (DIM == 3) ? 1.0 / S.d[1] : 0.0, iz = 1.0 / S.d[2];
+    const double* __restrict__ Ex = S.F[0];
+    const double* __restrict__ Ey = S.F[1];
+    const double* __restrict__ Ez = S.F[2];
+    double* __restrict__ Bx = S.F[3];
+    double* __restrict__ By = S.F[4];
+    double* __restrict__ Bz = S.F[5];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(c % nx);
+        int j = (int)((c / nx) % ny);
+        int k = (int)(c / ((int64_t)nx * ny));
+        int64_t o = pidx(S, i, j, k);
+        int64_t oi = pidx(S, nxt(i, nx), j, k);
+        int64_t oj = (DIM == 3) ? pidx(S, i, nxt(j, ny), k) : o;
+        int64_t ok = pidx(S, i, j, nxt(k, nz));
+        double ez = Ez[o], ey = Ey[o], ex = Ex[o];
+        double cEx = (Ez[oj] - ez) * iy - (Ey[ok] - ey) * iz;
+        double cEy = (Ex[ok] - ex) * iz - (Ez[oi] - ez) * ix;
+        double cEz = (Ey[oi] - ey) * ix - (Ex[oj] - ex) * iy;
+        Bx[o] -= h * cEx;
+        By[o] -= h * cEy;
+        Bz[o] -= h * cEz;
+    }
+}
+
+template <int DIM>
+__global__ void e_kernel(const SimDev* __restrict__ sims) {
+    const SimDev& S = sims[0];
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    const double dt = S.dt;
+    const double ix = 1.0 / S.d[0], iy = (DIM == 3) ? 1.0 / S.d[1] : 0.0, iz = 1.0 / S.d[2];
+    double* __restrict__ Ex = S.F[0];
+    double* __restrict__ Ey = S.F[1];
+    double* __restrict__ Ez = S.F[2];
+    const double* __restrict__ Bx = S.F[3];
+    const double* __restrict__ By = S.F[4];
+    const double* __restrict__ Bz = S.F[5];
+    const double* __restrict__ Jx = S.F[6];
+    const double* __restrict__ Jy = S.F[7];
+    const double* __restrict__ Jz = S.F[8];
+    const LaserDev L = S.las;
+    double amp = 0.0;
+    if (L.on) {
+        double t = ((double)(*S.step) + 0.5) * dt;
+        double tt = (t - L.t_peak) / L.tau;
+        amp = 2.0 * L.a0 / S.d[2] * exp(-tt * tt) * sin(L.omega * (t - L.t_peak));
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(c % nx);
+        int j = (int)((c / nx) % ny);
+        int k = (int)(c / ((int64_t)nx * ny));
+        int64_t o = pidx(S, i, j, k);
+        int64_t oi = pidx(S, prv(i, nx), j, k);
+        int64_t oj = (DIM == 3) ? pidx(S, i, prv(j, ny), k) : o;
+        int64_t ok = pidx(S, i, j, prv(k, nz));
+        double bx = Bx[o], by = By[o], bz = Bz[o];
+        double cBx = (bz - Bz[oj]) * iy - (by - By[ok]) * iz;
+        double cBy = (bx - Bx[ok]) * iz - (bz - Bz[oi]) * ix;
+        double cBz = (by - By[oi]) * ix - (bx - Bx[oj]) * iy;
+        double jx = Jx[o];
+        if (L.on && k == L.k_ant) {
+            double x = ((double)i + 0.5) * S.d[0] - L.xc;
+            double y = (DIM == 3) ? (double)j * S.d[1] - L.yc : 0.0;
+            jx += amp * exp(-(x * x + y * y) / (L.w0 * L.w0));
+            const_cast<double*>(Jx)[o] = jx;  // the antenna sheet is part of J^{n+1/2}
+        }
+        Ex[o] += dt * (cBx - jx);
+        Ey[o] += dt * (cBy - Jy[o]);
+        Ez[o] += dt * (cBz - Jz[o]);
+    }
+}
+
+// E and B of cell layer k scaled by 1 - 0.5 (p/A)^2, p = depth inside the layer
+__global__ void damp_kernel(const SimDev* __restrict__ sims) {
+    const SimDev& S = sims[0];
+    const int A = S.absorb;
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const int64_t per_layer = (int64_t)nx * ny;
+    const int64_t total = per_layer * 2 * A;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int layer = (int)(c / per_layer);
+        int64_t r = c - (int64_t)layer * per_layer;
+        int i = (int)(r % nx), j = (int)(r / nx);
+        int k = layer < A ? layer : nz - 2 * A + layer;
+        int p = k < A ? A - k : k - (nz - 1 - A);
+        double q = (double)p / (double)A;
+        double f = 1.0 - 0.5 * q * q;
+        int64_t o = pidx(S, i, j, k);
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp) S.F[comp][o] *= f;
+    }
+}
+
+// periodic images into the guard cells of components [c0, c0+nc)
+__global__ void guard_kernel(const SimDev* __restrict__ sims, int c0, int nc) {
+    const SimDev& S = sims[0];
+    const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
+    const int64_t pvol = (int64_t)px * py * pz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pvol;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int a = (int)(c % px);
+        int b = (int)((c / px) % py);
+        int e = (int)(c / ((int64_t)px * py));
+        int i = a - S.g[0], j = b - S.g[1], k = e - S.g[2];
+        bool inside = (i >= 0 && i < S.n[0]) && (j >= 0 && j < S.n[1]) && (k >= 0 && k < S.n[2]);
+        if (inside) continue;
+        int si = ((i % S.n[0]) + S.n[0]) % S.n[0];
+        int sj = ((j % S.n[1]) + S.n[1]) % S.n[1];
+        int sk = ((k % S.n[2]) + S.n[2]) % S.n[2];
+        int64_t src = pidx(S, si, sj, sk);
+        for (int comp = c0; comp < c0 + nc; ++comp) S.F[comp][c] = S.F[comp][src];
+    }
+}
+
+__global__ void unpad_kernel(const double* __restrict__ src, double* __restrict__ dst, SimDev S) {
+    const int64_t ncell = (int64_t)S.n[0] * S.n[1] * S.n[2];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(c % S.n[0]);
+        int j = (int)((c / S.n[0]) % S.n[1]);
+        int k = (int)(c / ((int64_t)S.n[0] * S.n[1]));
+        dst[c] = src[pidx(S, i, j, k)];
+    }
+}
+
+__global__ void pad_kernel(const double* __restrict__ src, double* __restrict__ dst, SimDev S) {
+    const int64_t ncell = (int64_t)S.n[0] * S.n[1] * S.n[2];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(c % S.n[0]);
+        int j = (int)((c / S.n[0]) % S.n[1]);
+        int k = (int)(c / ((int64_t)S.n[0] * S.n[1]));
+        dst[pidx(S, i, j, k)] = src[c];
+    }
+}
+
+// charge density at the nodes (diagnostic): shape S of the run's order
+template <int DIM, int ORDER>
+__global__ void rho_kernel(const SimDev* __restrict__ sims, int sp_idx, double* __restrict__ rho) {
+    const SimDev& S = sims[0];
+    const SpeciesDev& sp = S.sp[sp_idx];
+    const int64_t np = sp.off[S.ntiles];
+    const double inv_vol = 1.0 / (S.d[0] * S.d[1] * S.d[2]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double X[3] = {sp.cur[0][p], DIM == 3 ? sp.cur[1][p] : 0.0, sp.cur[2][p]};
+        int s[3];
+        double w[3][3];
+        for (int a = 0; a < 3; ++a) {
+            if (DIM == 2 && a == 1) { s[a] = 0; w[a][0] = 1.0; continue; }
+            if (ORDER == 1) {
+                s[a] = (int)floor(X[a]);
+                double f = X[a] - s[a];
+                w[a][0] = 1.0 - f;
+                w[a][1] = f;
+            } else {
+                int c = (int)floor(X[a] + 0.5);
+                double d = X[a] - c;
+                s[a] = c - 1;
+                w[a][0] = 0.5 * (0.5 - d) * (0.5 - d);
+                w[a][1] = 0.75 - d * d;
+                w[a][2] = 0.5 * (0.5 + d) * (0.5 + d);
+            }
+        }
+        const double qw = sp.q * sp.cur[6][p] * inv_vol;
+        const int ny_pts = (DIM == 3) ? ORDER + 1 : 1;
+        for (int c = 0; c <= ORDER; ++c)
+            for (int b = 0; b < ny_pts; ++b)
+                for (int a = 0; a <= ORDER; ++a) {
+                    int i = ((s[0] + a) % S.n[0] + S.n[0]) % S.n[0];
+                    int j = (DIM == 3) ? ((s[1] + b) % S.n[1] + S.n[1]) % S.n[1] : 0;
+                    int k = ((s[2] + c) % S.n[2] + S.n[2]) % S.n[2];
+                    atomicAdd(rho + ((int64_t)k * S.n[1] + j) * S.n[0] + i,
+                              qw * w[0][a] * w[1][b] * w[2][c]);
+                }
+    }
+}
+
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+int blocks_for(int64_t n, int t) {
+    int64_t b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t st) {
+    const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
+    const int nb = blocks_for(ncell, 256);
+    if (h.dim == 3) {
+        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim);
+        e_kernel<3><<<nb, 256, 0, st>>>(dsim);
+        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim);
+    } else {
+        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim);
+        e_kernel<2><<<nb, 256, 0, st>>>(dsim);
+        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim);
+    }
+    if (h.absorb > 0) {
+        int64_t t = (int64_t)h.n[0] * h.n[1] * 2 * h.absorb;
+        damp_kernel<<<blocks_for(t, 256), 256, 0, st>>>(dsim);
+    }
+    return pic_launch_guards(dsim, h, 0, 6, st);
+}
+
+cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& h, int c0, int nc,
+                              cudaStream_t st) {
+    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
+    guard_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, c0, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_unpad(const double* padded, double* dense, const SimDev& h,
+                             cudaStream_t st) {
+    const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
+    unpad_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(padded, dense, h);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_pad(const double* dense, double* padded, const SimDev& h,
+                           cudaStream_t st) {
+    const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
+    pad_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(dense, padded, h);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_rho(const SimDev* dsim, const SimDev& h, double* rho, double rho0,
+                           cudaStream_t st) {
+    const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
+    fill_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(rho, ncell, rho0);
+    for (int s = 0; s < h.nsp; ++s) {
+        int64_t cap = h.sp[s].cap;
+        int nb = blocks_for(cap, 256);
+        if (h.dim == 3 && h.order == 1) rho_kernel<3, 1><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else if (h.dim == 3) rho_kernel<3, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else if (h.order == 1) rho_kernel<2, 1><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else rho_kernel<2, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,126 @@
+// pic_internal.h -- device-side data layout of libpic (shared by the .cu files
+// of the library only; the CPU oracle never includes it).
+//
+// HBM layout of one simulation:
+//   fields  9 FP64 arrays (Ex Ey Ez Bx By Bz Jx Jy Jz), each padded by guard
+//           cells in every active direction (3 per side in x, 2 in y and z):
+//           dims (nx+6, ny+4, nz+4), x fastest (ny+4 -> 1 in 2D).  Guards of E and B hold the
+//           periodic images after every step, so a tile plus its halo is one
+//           rectangular TMA box; J guards stay zero (the deposit flush wraps
+//           indices itself).  J is one contiguous block of 3 arrays.
+//   particles per species, SoA of FP64 X Y Z (global cell units, X = x/dx),
+//           ux uy uz (u = gamma v), w, plus int64 id; double-buffered, sorted
+//           by tile (tiles numbered box-major, so each box is contiguous).
+//   sort    per species: key[cap] (tile of the new position), count and
+//           cursor[ntiles+1], off[ntiles+2] (exclusive scan of count).
+//   costs   uint64 cost_clock[nboxes] (summed thread clocks), per simulation.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PIC_G 2        // guard cells per side in y and z of the padded field arrays
+#define PIC_GX 3       // guard cells per side in x: odd, so that a tile's TMA box, which
+                       // starts one cell below an even tile origin, starts at an even
+                       // padded x (x * 8 bytes must be a multiple of 16)
+#define PIC_MAXSP 4    // species per simulation
+#define PIC_NCOMP 9
+
+// error codes written by kernels into the device error word
+#define PIC_DERR_TMA_TIMEOUT 1
+#define PIC_DERR_BOUNDS 2
+#define PIC_DERR_SCATTER 4
+
+struct SpeciesDev {
+    double q, m;
+    double kq;            // q dt / (2 m): half electric kick factor
+    double qw_scale;      // q / (dV dt)-style deposit prefactor (per simulation dims)
+    double* cur[7];       // X Y Z ux uy uz w  (current, tile-sorted)
+    double* alt[7];       // scatter target
+    int64_t* id;
+    int64_t* id_alt;
+    int32_t* key;         // [cap]
+    int32_t* count;       // [ntiles+1]
+    int32_t* cursor;      // [ntiles+1]
+    int64_t* off;         // [ntiles+2]; off[ntiles] = particles kept
+    int64_t* np_prev;     // particles in the buffer being scattered
+    int64_t cap;
+};
+
+struct LaserDev {
+    int on;
+    int k_ant;
+    double a0, w0, tau, t_peak, omega, xc, yc;
+};
+
+struct SimDev {
+    CUtensorMap tmap[6];  // TMA descriptors of the padded E,B arrays (must stay first)
+    int dim, order, nsp, absorb;
+    int n[3];             // cells per direction
+    int pn[3];            // padded extents (n + 2G; 1 for an inactive y)
+    int g[3];             // guard width per direction (G or 0)
+    int T[3];             // tile extents in cells (T[1] = 1 in 2D)
+    int tpb[3];           // tiles per box per direction
+    int nb[3];            // boxes per direction
+    int bsz[3];           // box extents in cells
+    int tiles_per_box, nboxes, ntiles;
+    int ebs[3];           // E/B shared tile extents (x padded to even for TMA)
+    int js[3];            // J shared tile extents
+    int jlo;              // J tile starts jlo cells below the tile origin
+    double d[3];          // cell sizes
+    double dt;
+    double dtd[3];        // dt / d
+    double jfac[3];       // -1/(dA_perp dt) for the prefix currents (3D); 2D see kernel
+    double jyfac2d;       // 1/(dx dz) for the 2D out-of-plane current
+    double* F[PIC_NCOMP]; // padded field arrays
+    uint64_t* cost_clock; // [nboxes]
+    int64_t* step;        // device step counter
+    int32_t* err;         // device error word (shared with the schedule)
+    LaserDev las;
+    SpeciesDev sp[PIC_MAXSP];
+};
+
+struct UnitDev {
+    int32_t sim, box, chunk, nchunks;
+};
+
+struct SchedDev {
+    UnitDev* units;       // [cap_units]
+    int32_t* list_off;    // [nlists+1] start of each list in units
+    int32_t* head;        // [nlists] atomic pull counters
+    int32_t* meta;        // [0] = nlists, [1] = steal (0/1)
+    int32_t* err;         // device error word
+};
+
+// padded linear index of interior cell (i,j,k) of a simulation
+__host__ __device__ inline int64_t pidx(const SimDev& s, int i, int j, int k) {
+    return ((int64_t)(k + s.g[2]) * s.pn[1] + (j + s.g[1])) * s.pn[0] + (i + s.g[0]);
+}
+
+// ---- kernel launchers (defined in the .cu files) ----
+struct LaunchCfg {
+    int threads;
+    int ctas;
+};
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3]);
+cudaError_t pic_prepare_particles(int dim, int order, size_t smem);  // outside graph capture
+cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                 const SchedDev* sched, SimDev* sims, cudaStream_t st);
+cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& hsim, cudaStream_t st);
+cudaError_t pic_launch_sort(const SimDev* dsim, const SimDev& hsim, int sp, cudaStream_t st);
+cudaError_t pic_launch_initial_keys(const SimDev* dsim, const SimDev& hsim, int sp,
+                                    int64_t np, cudaStream_t st);
+cudaError_t pic_launch_finish(SimDev* dsim, const SchedDev* sched, cudaStream_t st);
+cudaError_t pic_launch_box_counts(const SimDev* dsim, const SimDev& hsim, int64_t* out,
+                                  cudaStream_t st);
+cudaError_t pic_launch_rho(const SimDev* dsim, const SimDev& hsim, double* rho, double rho0,
+                           cudaStream_t st);
+cudaError_t pic_launch_unpad(const double* padded, double* dense, const SimDev& hsim,
+                             cudaStream_t st);
+cudaError_t pic_launch_pad(const double* dense, double* padded, const SimDev& hsim,
+                           cudaStream_t st);
+cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& hsim, int first_comp,
+                              int ncomp, cudaStream_t st);
+cudaError_t pic_launch_to_cells(double* p, int64_t np, double d, int n, cudaStream_t st);
+cudaError_t pic_launch_from_cells(const double* src, double* dst, int64_t np, double d,
+                                  cudaStream_t st);

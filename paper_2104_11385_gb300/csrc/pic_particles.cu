@@ -1,0 +1,830 @@
+// pic_particles.cu -- the particle side of the PIC cycle on sm_103a.
+//
+// pic_particle_kernel: persistent CTAs pull work units (a chunk of one box's
+// particles) from cost-ordered lists.  For every tile (sub-box) a unit touches,
+// the guard-extended E/B tile is staged into shared memory by TMA
+// (cp.async.bulk.tensor, local HBM only, no multicast), the current is
+// deposited into a shared-memory J tile with shared FP64 atomics and flushed
+// once per tile into the global J arrays.  Each thread brackets its particle
+// loop with clock64(); the deltas are warp-reduced, summed in shared memory and
+// added once per unit to the box's cost -- the device-clock cost of
+// arXiv 2104.11385 Sec. 2.2 (Fig. 2a).  The same pass writes each particle's
+// new tile key and the per-tile histogram for the re-sort.
+//
+// Physics per particle (the schemes the paper leaves open, Sec. 2.1): field
+// gather with B-spline shapes at each component's Yee location, relativistic
+// Boris push, Esirkepov charge-conserving deposit (Esirkepov 2001).
+#include "pic_internal.h"
+
+namespace {
+
+constexpr double kThird = 1.0 / 3.0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of %globaltimer.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 0u) {
+            uint64_t now = globaltimer();
+            if (it == 0) t0 = now;
+            else if (now - t0 > 2000000000ull) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// one-dimensional B-spline support: first node and ORDER+1 weights
+template <int ORDER>
+struct Support {
+    int s;
+    double w[ORDER + 1];
+};
+
+template <int ORDER>
+__device__ __forceinline__ Support<ORDER> support(double xi) {
+    Support<ORDER> r;
+    if (ORDER == 1) {
+        r.s = __double2int_rd(xi);
+        double f = xi - (double)r.s;
+        r.w[0] = 1.0 - f;
+        r.w[1] = f;
+    } else {
+        int c = __double2int_rd(xi + 0.5);
+        double d = xi - (double)c;  // in [-1/2, 1/2)
+        double a = 0.5 - d, b = 0.5 + d;
+        r.s = c - 1;
+        r.w[0] = 0.5 * a * a;
+        r.w[1] = 0.75 - d * d;
+        r.w[ORDER] = 0.5 * b * b;
+    }
+    return r;
+}
+
+// interpolation of one component from a shared tile with extents (SX, SY)
+template <int ORDER, int DIM>
+__device__ __forceinline__ double interp(const double* __restrict__ F, int SX, int SY,
+                                         const Support<ORDER>& sx, const Support<ORDER>& sy,
+                                         const Support<ORDER>& sz) {
+    // tile column 0 is local cell -1
+    if (DIM == 3) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c <= ORDER; ++c) {
+            double pl = 0.0;
+#pragma unroll
+            for (int b = 0; b <= ORDER; ++b) {
+                const double* row = F + ((sz.s + 1 + c) * SY + (sy.s + 1 + b)) * SX + (sx.s + 1);
+                double r = sx.w[0] * row[0];
+#pragma unroll
+                for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
+                pl = (b == 0) ? sy.w[0] * r : fma(sy.w[b], r, pl);
+            }
+            acc = (c == 0) ? sz.w[0] * pl : fma(sz.w[c], pl, acc);
+        }
+        return acc;
+    } else {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c <= ORDER; ++c) {
+            const double* row = F + (sz.s + 1 + c) * SX + (sx.s + 1);
+            double r = sx.w[0] * row[0];
+#pragma unroll
+            for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
+            acc = (c == 0) ? sz.w[0] * r : fma(sz.w[c], r, acc);
+        }
+        return acc;
+    }
+}
+
+// Esirkepov node shapes on the common window of W = ORDER + 2 nodes that
+// starts at the lower of the two supports.
+template <int ORDER>
+struct Window {
+    int base;
+    double S0[ORDER + 2];
+    double DS[ORDER + 2];
+};
+
+template <int ORDER>
+__device__ __forceinline__ bool make_window(const Support<ORDER>& a, const Support<ORDER>& b,
+                                            Window<ORDER>& win) {
+    constexpr int W = ORDER + 2;
+    int base = min(a.s, b.s);
+    int oa = a.s - base, ob = b.s - base;  // 0 or 1 when the move is below one cell
+    if ((oa | ob) & ~1) return false;
+    win.base = base;
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int k = 0; k <= ORDER; ++k) {
+            s0 = (l - oa == k) ? a.w[k] : s0;
+            s1 = (l - ob == k) ? b.w[k] : s1;
+        }
+        win.S0[l] = s0;
+        win.DS[l] = s1 - s0;
+    }
+    return true;
+}
+
+struct Tile {
+    int sim;
+    int t;
+    int o[3];  // origin cell
+};
+
+__device__ __forceinline__ void tile_origin(const SimDev& S, int t, int o[3]) {
+    int b = t / S.tiles_per_box, lt = t - b * S.tiles_per_box;
+    int bx = b % S.nb[0], by = (b / S.nb[0]) % S.nb[1], bz = b / (S.nb[0] * S.nb[1]);
+    int tx = lt % S.tpb[0], ty = (lt / S.tpb[0]) % S.tpb[1], tz = lt / (S.tpb[0] * S.tpb[1]);
+    o[0] = bx * S.bsz[0] + tx * S.T[0];
+    o[1] = by * S.bsz[1] + ty * S.T[1];
+    o[2] = bz * S.bsz[2] + tz * S.T[2];
+}
+
+__device__ __forceinline__ int modi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+// tile key of a global cell (box-major numbering)
+__device__ __forceinline__ int tile_key(const SimDev& S, int ix, int iy, int iz) {
+    int bx = ix / S.bsz[0], by = iy / S.bsz[1], bz = iz / S.bsz[2];
+    int tx = (ix - bx * S.bsz[0]) / S.T[0];
+    int ty = (iy - by * S.bsz[1]) / S.T[1];
+    int tz = (iz - bz * S.bsz[2]) / S.T[2];
+    int b = (bz * S.nb[1] + by) * S.nb[0] + bx;
+    return b * S.tiles_per_box + (tz * S.tpb[1] + ty) * S.tpb[0] + tx;
+}
+
+__device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
+    unsigned act = __activemask();
+    unsigned peers = __match_any_sync(act, key);
+    int lane = threadIdx.x & 31;
+    if (lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+}
+
+// Shared-memory layout sizes for a tile configuration
+struct SmemPlan {
+    int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
+    int j_stride;   // doubles per J component
+    int eb_vol, j_vol;
+    size_t bytes;
+};
+
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3]) {
+    SmemPlan p;
+    p.eb_vol = ebs[0] * ebs[1] * ebs[2];
+    p.j_vol = js[0] * js[1] * js[2];
+    p.eb_stride = (p.eb_vol + 15) & ~15;
+    p.j_stride = p.j_vol;
+    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);
+    return p;
+}
+
+template <int DIM, int ORDER>
+__device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restrict__ sJ,
+                        const SmemPlan& P) {
+    const int jx = S.js[0], jy = S.js[1];
+    for (int idx = threadIdx.x; idx < 3 * P.j_vol; idx += blockDim.x) {
+        int comp = idx / P.j_vol, r = idx - comp * P.j_vol;
+        double v = sJ[comp * P.j_stride + r];
+        if (v == 0.0) continue;
+        int a = r % jx, b = (r / jx) % jy, c = r / (jx * jy);
+        int gx = modi(tl.o[0] - S.jlo + a, S.n[0]);
+        int gy = (DIM == 3) ? modi(tl.o[1] - S.jlo + b, S.n[1]) : 0;
+        int gz = modi(tl.o[2] - S.jlo + c, S.n[2]);
+        atomicAdd(S.F[6 + comp] + pidx(S, gx, gy, gz), v);
+    }
+}
+
+template <int DIM, int ORDER>
+__device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
+                                         const double* __restrict__ sEB, double* __restrict__ sJ,
+                                         const SmemPlan& P, int64_t p, int32_t* err) {
+    constexpr int W = ORDER + 2;
+    double X = sp.cur[0][p], Z = sp.cur[2][p];
+    double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
+    double u0 = sp.cur[3][p], u1 = sp.cur[4][p], u2 = sp.cur[5][p];
+    const double w = sp.cur[6][p];
+
+    const double xl = X - (double)tl.o[0];
+    const double yl = (DIM == 3) ? Y - (double)tl.o[1] : 0.0;
+    const double zl = Z - (double)tl.o[2];
+
+    // ---- gather at x^n: node and half-node supports per direction
+    Support<ORDER> nx = support<ORDER>(xl), hx = support<ORDER>(xl - 0.5);
+    Support<ORDER> nz = support<ORDER>(zl), hz = support<ORDER>(zl - 0.5);
+    Support<ORDER> ny, hy;
+    if (DIM == 3) {
+        ny = support<ORDER>(yl);
+        hy = support<ORDER>(yl - 0.5);
+    } else {
+        ny.s = -1; ny.w[0] = 1.0;
+        hy = ny;
+    }
+    {
+        // the particle must sit in its tile (local cell index in [0, T)):
+        // linear: node support start = floor(xl); quadratic: half-node
+        // support start = floor(xl) - 1
+        bool in;
+        if (ORDER == 1) {
+            in = nx.s >= 0 && nx.s < S.T[0] && nz.s >= 0 && nz.s < S.T[2];
+            if (DIM == 3) in = in && ny.s >= 0 && ny.s < S.T[1];
+        } else {
+            in = hx.s >= -1 && hx.s < S.T[0] - 1 && hz.s >= -1 && hz.s < S.T[2] - 1;
+            if (DIM == 3) in = in && hy.s >= -1 && hy.s < S.T[1] - 1;
+        }
+        if (!in) {
+            atomicOr(err, PIC_DERR_BOUNDS);
+            sp.key[p] = S.ntiles;
+            warp_hist_add(sp.count, S.ntiles);
+            return;
+        }
+    }
+    const int SX = S.ebs[0], SY = S.ebs[1];
+    const double* Ex = sEB;
+    const double* Ey = sEB + P.eb_stride;
+    const double* Ez = sEB + 2 * P.eb_stride;
+    const double* Bx = sEB + 3 * P.eb_stride;
+    const double* By = sEB + 4 * P.eb_stride;
+    const double* Bz = sEB + 5 * P.eb_stride;
+    double e0 = interp<ORDER, DIM>(Ex, SX, SY, hx, ny, nz);
+    double e1 = interp<ORDER, DIM>(Ey, SX, SY, nx, hy, nz);
+    double e2 = interp<ORDER, DIM>(Ez, SX, SY, nx, ny, hz);
+    double b0 = interp<ORDER, DIM>(Bx, SX, SY, nx, hy, hz);
+    double b1 = interp<ORDER, DIM>(By, SX, SY, hx, ny, hz);
+    double b2 = interp<ORDER, DIM>(Bz, SX, SY, hx, hy, nz);
+
+    // ---- relativistic Boris push
+    const double k = sp.kq;
+    double m0 = fma(k, e0, u0), m1 = fma(k, e1, u1), m2 = fma(k, e2, u2);
+    double ig = rsqrt(1.0 + m0 * m0 + m1 * m1 + m2 * m2);
+    double kg = k * ig;
+    double t0 = kg * b0, t1 = kg * b1, t2 = kg * b2;
+    double t2n = t0 * t0 + t1 * t1 + t2 * t2;
+    double sf = 2.0 / (1.0 + t2n);
+    double s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
+    double d0 = m0 + (m1 * t2 - m2 * t1);
+    double d1 = m1 + (m2 * t0 - m0 * t2);
+    double d2 = m2 + (m0 * t1 - m1 * t0);
+    double p0 = m0 + (d1 * s2 - d2 * s1);
+    double p1 = m1 + (d2 * s0 - d0 * s2);
+    double p2 = m2 + (d0 * s1 - d1 * s0);
+    u0 = fma(k, e0, p0);
+    u1 = fma(k, e1, p1);
+    u2 = fma(k, e2, p2);
+    double ign = rsqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2);
+    double v0 = u0 * ign, v1 = u1 * ign, v2 = u2 * ign;
+    double dX = v0 * S.dtd[0], dZ = v2 * S.dtd[2];
+    double dY = (DIM == 3) ? v1 * S.dtd[1] : 0.0;
+
+    // ---- Esirkepov deposit of J^{n+1/2} from x^n to x^{n+1}
+    const double x1l = xl + dX, z1l = zl + dZ;
+    Support<ORDER> mx = support<ORDER>(x1l), mz = support<ORDER>(z1l);
+    Window<ORDER> wx, wz, wy;
+    bool ok = make_window<ORDER>(nx, mx, wx) && make_window<ORDER>(nz, mz, wz);
+    if (DIM == 3) {
+        Support<ORDER> my = support<ORDER>(yl + dY);
+        ok = ok && make_window<ORDER>(ny, my, wy);
+    }
+    if (!ok) {
+        atomicOr(err, PIC_DERR_BOUNDS);
+        sp.key[p] = S.ntiles;
+        warp_hist_add(sp.count, S.ntiles);
+        return;
+    }
+    const double qw = sp.q * w;
+    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    double* Jx = sJ;
+    double* Jy = sJ + P.j_stride;
+    double* Jz = sJ + 2 * P.j_stride;
+    double Ax[W], Cx[W], Az[W], Cz[W];
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        Ax[l] = fma(0.5, wx.DS[l], wx.S0[l]);
+        Cx[l] = fma(kThird, wx.DS[l], 0.5 * wx.S0[l]);
+        Az[l] = fma(0.5, wz.DS[l], wz.S0[l]);
+        Cz[l] = fma(kThird, wz.DS[l], 0.5 * wz.S0[l]);
+    }
+    if (DIM == 3) {
+        double Ay[W], Cy[W];
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            Ay[l] = fma(0.5, wy.DS[l], wy.S0[l]);
+            Cy[l] = fma(kThird, wy.DS[l], 0.5 * wy.S0[l]);
+        }
+        const int bx = wx.base + lo, by = wy.base + lo, bz = wz.base + lo;
+        // Jx: prefix sum along x of DSx, times the (y,z) weight
+        {
+            const double c = qw * S.jfac[0];
+            double P_[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; P_[l] = c * acc; }
+#pragma unroll
+            for (int n = 0; n < W; ++n)
+#pragma unroll
+                for (int m = 0; m < W; ++m) {
+                    double T = fma(Ay[m], wz.S0[n], Cy[m] * wz.DS[n]);
+                    double* row = Jx + ((bz + n) * jy + (by + m)) * jx + bx;
+#pragma unroll
+                    for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, P_[l] * T);
+                }
+        }
+        {
+            const double c = qw * S.jfac[1];
+            double P_[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int m = 0; m < W - 1; ++m) { acc += wy.DS[m]; P_[m] = c * acc; }
+#pragma unroll
+            for (int n = 0; n < W; ++n)
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    double T = fma(Ax[l], wz.S0[n], Cx[l] * wz.DS[n]);
+                    double* col = Jy + ((bz + n) * jy + by) * jx + (bx + l);
+#pragma unroll
+                    for (int m = 0; m < W - 1; ++m) atomicAdd(col + m * jx, P_[m] * T);
+                }
+        }
+        {
+            const double c = qw * S.jfac[2];
+            double P_[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int n = 0; n < W - 1; ++n) { acc += wz.DS[n]; P_[n] = c * acc; }
+#pragma unroll
+            for (int m = 0; m < W; ++m)
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    double T = fma(Ax[l], wy.S0[m], Cx[l] * wy.DS[m]);
+                    double* col = Jz + (bz * jy + (by + m)) * jx + (bx + l);
+#pragma unroll
+                    for (int n = 0; n < W - 1; ++n) atomicAdd(col + n * jx * jy, P_[n] * T);
+                }
+        }
+    } else {
+        const int bx = wx.base + lo, bz = wz.base + lo;
+        {  // Jx(l,n) = -(q w /(dz dt)) sum_{l'<=l} DSx(l') (S0z + DSz/2)
+            const double c = qw * S.jfac[0];
+            double P_[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; P_[l] = c * acc; }
+#pragma unroll
+            for (int n = 0; n < W; ++n) {
+                double* row = Jx + (bz + n) * jx + bx;
+#pragma unroll
+                for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, P_[l] * Az[n]);
+            }
+        }
+        {
+            const double c = qw * S.jfac[2];
+            double P_[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int n = 0; n < W - 1; ++n) { acc += wz.DS[n]; P_[n] = c * acc; }
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+                double* col = Jz + bz * jx + (bx + l);
+#pragma unroll
+                for (int n = 0; n < W - 1; ++n) atomicAdd(col + n * jx, P_[n] * Ax[l]);
+            }
+        }
+        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax S0z + Cx DSz)
+            const double c = qw * v1 * S.jyfac2d;
+#pragma unroll
+            for (int n = 0; n < W; ++n)
+#pragma unroll
+                for (int l = 0; l < W; ++l)
+                    atomicAdd(Jy + (bz + n) * jx + (bx + l),
+                              c * fma(Ax[l], wz.S0[n], Cx[l] * wz.DS[n]));
+        }
+    }
+
+    // ---- new position, boundary, re-sort key
+    X += dX;
+    Z += dZ;
+    if (X < 0.0) X += (double)S.n[0];
+    if (X >= (double)S.n[0]) X -= (double)S.n[0];
+    if (DIM == 3) {
+        Y += dY;
+        if (Y < 0.0) Y += (double)S.n[1];
+        if (Y >= (double)S.n[1]) Y -= (double)S.n[1];
+    }
+    int key;
+    if (S.absorb > 0) {
+        if (Z < (double)S.absorb || Z >= (double)(S.n[2] - S.absorb)) key = S.ntiles;
+        else key = -1;
+    } else {
+        if (Z < 0.0) Z += (double)S.n[2];
+        if (Z >= (double)S.n[2]) Z -= (double)S.n[2];
+        key = -1;
+    }
+    if (key < 0) {
+        int ix = min(__double2int_rd(X), S.n[0] - 1);
+        int iy = (DIM == 3) ? min(__double2int_rd(Y), S.n[1] - 1) : 0;
+        int iz = min(__double2int_rd(Z), S.n[2] - 1);
+        key = tile_key(S, ix, iy, iz);
+    }
+    sp.cur[0][p] = X;
+    if (DIM == 3) sp.cur[1][p] = Y;
+    sp.cur[2][p] = Z;
+    sp.cur[3][p] = u0;
+    sp.cur[4][p] = u1;
+    sp.cur[5][p] = u2;
+    sp.key[p] = key;
+    warp_hist_add(sp.count, key);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace
+
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) pic_particle_kernel(const SchedDev* __restrict__ sd,
+                                                           SimDev* __restrict__ sims) {
+    extern __shared__ __align__(128) double smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    // TMA destinations must be 128-byte aligned: round the dynamic base up
+    double* smem = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    __shared__ int s_unit, s_list, s_abort;
+    __shared__ unsigned long long s_cost;
+
+    const int nlists = sd->meta[0];
+    const int steal = sd->meta[1];
+    const int my_list = blockIdx.x % nlists;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        s_list = my_list;
+        s_abort = 0;
+        s_cost = 0ull;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    Tile cur;
+    cur.sim = -1;
+    cur.t = -1;
+    int visited = 0;
+
+    while (true) {
+        if (threadIdx.x == 0) {
+            int u = -1;
+            while (visited < nlists) {
+                int L = s_list;
+                int pos = atomicAdd(sd->head + L, 1);
+                int b = sd->list_off[L], e = sd->list_off[L + 1];
+                if (b + pos < e) { u = b + pos; break; }
+                if (!steal) { visited = nlists; break; }
+                s_list = (L + 1) % nlists;
+                ++visited;
+            }
+            s_unit = u;
+        }
+        __syncthreads();
+        const int u = s_unit;
+        if (u < 0) break;
+        const UnitDev unit = sd->units[u];
+        const SimDev& S = sims[unit.sim];
+        const SmemPlan P = smem_plan(S.ebs, S.js);
+        double* sEB = smem;
+        double* sJ = smem + 6 * P.eb_stride;
+        unsigned long long my_clk = 0ull;
+
+        for (int spi = 0; spi < S.nsp; ++spi) {
+            const SpeciesDev& sp = S.sp[spi];
+            const int t_first = unit.box * S.tiles_per_box;
+            const int t_end = t_first + S.tiles_per_box;
+            const int64_t b0 = sp.off[t_first], nbp = sp.off[t_end] - b0;
+            const int64_t r0 = b0 + (nbp * unit.chunk) / unit.nchunks;
+            const int64_t r1 = b0 + (nbp * (unit.chunk + 1)) / unit.nchunks;
+            if (r0 >= r1) continue;
+            for (int t = t_first; t < t_end; ++t) {
+                const int64_t s0 = max(sp.off[t], r0), s1 = min(sp.off[t + 1], r1);
+                if (s0 >= s1) continue;
+                if (t != cur.t || unit.sim != cur.sim) {
+                    __syncthreads();
+                    if (cur.t >= 0) {
+                        const SimDev& CS = sims[cur.sim];
+                        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
+                        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+                        __syncthreads();
+                    }
+                    cur.sim = unit.sim;
+                    cur.t = t;
+                    tile_origin(S, t, cur.o);
+                    if (threadIdx.x == 0) {
+                        fence_proxy_async();
+                        mbar_expect_tx(&bar, (uint32_t)(6 * P.eb_vol * sizeof(double)));
+                        const int x0 = cur.o[0] - 1 + S.g[0];
+                        const int y0 = (DIM == 3) ? cur.o[1] - 1 + S.g[1] : 0;
+                        const int z0 = cur.o[2] - 1 + S.g[2];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c)
+                            tma_load_3d(sEB + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
+                    }
+                    for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJ[i] = 0.0;
+                    bool ok = mbar_wait_bounded(&bar, phase);
+                    phase ^= 1u;
+                    if (!ok) {
+                        atomicOr(sd->err, PIC_DERR_TMA_TIMEOUT);
+                        atomicExch(&s_abort, 1);
+                    }
+                    __syncthreads();
+                    if (s_abort) {
+                        // the copies may still be in flight: one more bounded wait, then leave
+                        if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase ^ 1u);
+                        __syncthreads();
+                        return;
+                    }
+                }
+                const unsigned long long c0 = clock64();
+                for (int64_t p = s0 + threadIdx.x; p < s1; p += blockDim.x)
+                    push_one<DIM, ORDER>(S, sp, cur, sEB, sJ, P, p, sd->err);
+                my_clk += clock64() - c0;
+            }
+        }
+        // in-situ cost: thread clocks -> warp sum -> shared -> one global add per unit
+        unsigned long long ws = warp_sum_u64(my_clk);
+        if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&s_cost, ws);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cost) atomicAdd((unsigned long long*)(S.cost_clock + unit.box), s_cost);
+            s_cost = 0ull;
+        }
+    }
+    if (cur.t >= 0) {
+        __syncthreads();
+        const SimDev& CS = sims[cur.sim];
+        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
+        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// re-sort: scan of the per-tile histogram, scatter, end-of-step bookkeeping
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) pic_scan_kernel(SimDev* __restrict__ sims, int sp_idx) {
+    SimDev& S = sims[0];
+    SpeciesDev& sp = S.sp[sp_idx];
+    const int N = S.ntiles + 1;  // tiles plus the bucket of removed particles
+    __shared__ int64_t s_part[1024];
+    __shared__ int64_t s_np_prev;
+    if (threadIdx.x == 0) s_np_prev = sp.off[S.ntiles];  // kept count of the buffer just pushed
+    const int per = (N + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per, i1 = min(N, i0 + per);
+    int64_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += sp.count[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    // inclusive Hillis-Steele scan of the partial sums
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int64_t v = (threadIdx.x >= (unsigned)o) ? s_part[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = s_part[threadIdx.x] - sum;
+    for (int i = i0; i < i1; ++i) {
+        int c = sp.count[i];
+        sp.off[i] = run;
+        run += c;
+        sp.count[i] = 0;
+        sp.cursor[i] = 0;
+    }
+    if (threadIdx.x == blockDim.x - 1) sp.off[N] = s_part[blockDim.x - 1];
+    if (threadIdx.x == 0) *sp.np_prev = s_np_prev;
+}
+
+template <int DIM>
+__global__ void pic_scatter_kernel(SimDev* __restrict__ sims, int sp_idx) {
+    const SimDev& S = sims[0];
+    const SpeciesDev& sp = S.sp[sp_idx];
+    const int64_t np = *sp.np_prev;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < np; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= np) break;
+        const int k = sp.key[p];
+        if (k < 0 || k > S.ntiles) {
+            atomicOr(S.err, PIC_DERR_SCATTER);
+            continue;
+        }
+        if (k == S.ntiles) continue;  // removed by the absorbing boundary
+        unsigned act = __activemask();
+        unsigned peers = __match_any_sync(act, k);
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(sp.cursor + k, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        const int64_t dst = sp.off[k] + base + rank;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) {
+            if (DIM == 2 && a == 1) continue;
+            sp.alt[a][dst] = sp.cur[a][p];
+        }
+        sp.id_alt[dst] = sp.id[p];
+    }
+}
+
+__global__ void pic_swap_kernel(SimDev* __restrict__ sims, int sp_idx) {
+    SpeciesDev& sp = sims[0].sp[sp_idx];
+    for (int a = 0; a < 7; ++a) {
+        double* t = sp.cur[a];
+        sp.cur[a] = sp.alt[a];
+        sp.alt[a] = t;
+    }
+    int64_t* ti = sp.id;
+    sp.id = sp.id_alt;
+    sp.id_alt = ti;
+}
+
+__global__ void pic_finish_kernel(SimDev* __restrict__ sims, const SchedDev* __restrict__ sd) {
+    const int nlists = sd->meta[0];
+    for (int i = threadIdx.x; i < nlists; i += blockDim.x) sd->head[i] = 0;
+    if (threadIdx.x == 0) *sims[0].step += 1;
+}
+
+template <int DIM>
+__global__ void pic_initial_keys_kernel(SimDev* __restrict__ sims, int sp_idx, int64_t np) {
+    const SimDev& S = sims[0];
+    const SpeciesDev& sp = S.sp[sp_idx];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < np; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= np) break;
+        int ix = min(max(__double2int_rd(sp.cur[0][p]), 0), S.n[0] - 1);
+        int iy = (DIM == 3) ? min(max(__double2int_rd(sp.cur[1][p]), 0), S.n[1] - 1) : 0;
+        int iz = min(max(__double2int_rd(sp.cur[2][p]), 0), S.n[2] - 1);
+        int key = tile_key(S, ix, iy, iz);
+        sp.key[p] = key;
+        warp_hist_add(sp.count, key);
+    }
+}
+
+__global__ void pic_box_counts_kernel(const SimDev* __restrict__ sims, int64_t* out) {
+    const SimDev& S = sims[0];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < S.nboxes; b += gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int s = 0; s < S.nsp; ++s)
+            c += S.sp[s].off[(b + 1) * S.tiles_per_box] - S.sp[s].off[b * S.tiles_per_box];
+        out[b] = c;
+    }
+}
+
+// physical position -> global cell units X = x / d, wrapped into [0, n)
+__global__ void pic_to_cells_kernel(double* p, int64_t np, double d, int n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double X = p[i] / d;
+        if (X < 0.0) X += (double)n;
+        if (X >= (double)n) X -= (double)n;
+        p[i] = X;
+    }
+}
+
+__global__ void pic_scale_copy_kernel(const double* __restrict__ s, double* __restrict__ d,
+                                      int64_t n, double f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i] * f;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3]) {
+    int ebs[3], js[3];
+    for (int a = 0; a < 3; ++a) {
+        bool act = !(dim == 2 && a == 1);
+        ebs[a] = act ? T[a] + (order == 1 ? 2 : 3) : 1;
+        js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
+    }
+    if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
+    return smem_plan(ebs, js).bytes + 128;  // + alignment slack of the dynamic base
+}
+
+template <int DIM, int ORDER>
+static cudaError_t launch_particles_t(const LaunchCfg& cfg, size_t smem, const SchedDev* sched,
+                                      SimDev* sims, cudaStream_t st) {
+    pic_particle_kernel<DIM, ORDER><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
+    const int b = (int)smem;
+    if (dim == 3 && order == 1)
+        return cudaFuncSetAttribute(pic_particle_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 3 && order == 2)
+        return cudaFuncSetAttribute(pic_particle_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 2 && order == 1)
+        return cudaFuncSetAttribute(pic_particle_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 2 && order == 2)
+        return cudaFuncSetAttribute(pic_particle_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                 const SchedDev* sched, SimDev* sims, cudaStream_t st) {
+    if (dim == 3 && order == 1) return launch_particles_t<3, 1>(cfg, smem, sched, sims, st);
+    if (dim == 3 && order == 2) return launch_particles_t<3, 2>(cfg, smem, sched, sims, st);
+    if (dim == 2 && order == 1) return launch_particles_t<2, 1>(cfg, smem, sched, sims, st);
+    if (dim == 2 && order == 2) return launch_particles_t<2, 2>(cfg, smem, sched, sims, st);
+    return cudaErrorInvalidValue;
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+cudaError_t pic_launch_sort(const SimDev* dsim, const SimDev& hsim, int sp, cudaStream_t st) {
+    SimDev* d = const_cast<SimDev*>(dsim);
+    pic_scan_kernel<<<1, 1024, 0, st>>>(d, sp);
+    int64_t cap = hsim.sp[sp].cap;
+    if (hsim.dim == 3) pic_scatter_kernel<3><<<grid_for(cap, 256), 256, 0, st>>>(d, sp);
+    else pic_scatter_kernel<2><<<grid_for(cap, 256), 256, 0, st>>>(d, sp);
+    pic_swap_kernel<<<1, 1, 0, st>>>(d, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_initial_keys(const SimDev* dsim, const SimDev& hsim, int sp, int64_t np,
+                                    cudaStream_t st) {
+    SimDev* d = const_cast<SimDev*>(dsim);
+    if (np > 0) {
+        if (hsim.dim == 3) pic_initial_keys_kernel<3><<<grid_for(np, 256), 256, 0, st>>>(d, sp, np);
+        else pic_initial_keys_kernel<2><<<grid_for(np, 256), 256, 0, st>>>(d, sp, np);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_finish(SimDev* dsim, const SchedDev* sched, cudaStream_t st) {
+    pic_finish_kernel<<<1, 256, 0, st>>>(dsim, sched);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_box_counts(const SimDev* dsim, const SimDev& hsim, int64_t* out,
+                                  cudaStream_t st) {
+    pic_box_counts_kernel<<<grid_for(hsim.nboxes, 256), 256, 0, st>>>(dsim, out);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_to_cells(double* p, int64_t np, double d, int n, cudaStream_t st) {
+    if (np > 0) pic_to_cells_kernel<<<grid_for(np, 256), 256, 0, st>>>(p, np, d, n);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_from_cells(const double* src, double* dst, int64_t np, double d,
+                                  cudaStream_t st) {
+    if (np > 0) pic_scale_copy_kernel<<<grid_for(np, 256), 256, 0, st>>>(src, dst, np, d);
+    return cudaGetLastError();
+}

@@ -1,0 +1,220 @@
+"""Thin Python wrapper over libpic's C ABI (same names as include/pic_api.h).
+
+Marshalling only: numpy arrays become host pointers, torch CUDA tensors become
+device pointers; every step of the PIC path runs in libpic's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        if a.dtype.is_floating_point:
+            import torch
+            assert a.dtype == torch.float64, "particle and field arrays are float64"
+        t = a.contiguous()
+        return ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, t
+    arr = np.ascontiguousarray(a)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+class Simulation:
+    """One libpic simulation (pic_init ... pic_destroy)."""
+
+    def __init__(self, dim, ncell, box, dx, dt=0.0, cfl=0.99, shape_order=1, absorb_cells=0,
+                 stream=None):
+        self._lib = L.load()
+        d = L.GridDesc()
+        d.dim = int(dim)
+        for a in range(3):
+            d.ncell[a] = int(ncell[a])
+            d.box[a] = int(box[a])
+            d.dx[a] = float(dx[a])
+        d.dt = float(dt)
+        d.cfl = float(cfl)
+        d.shape_order = int(shape_order)
+        d.absorb_cells = int(absorb_cells)
+        d.stream = ctypes.c_void_p(stream) if stream else None
+        h = ctypes.c_void_p()
+        L.check(self._lib.pic_init(ctypes.byref(d), ctypes.byref(h)), None)
+        self._h = h
+        self.dim = int(dim)
+        self.ncell = tuple(int(v) for v in ncell)
+        self.box = tuple(int(v) for v in box)
+        self.dx = tuple(float(v) for v in dx)
+        self.nspecies = 0
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        L.check(st, self._h)
+
+    @property
+    def ncells_total(self):
+        return self.ncell[0] * self.ncell[1] * self.ncell[2]
+
+    @property
+    def nboxes(self):
+        return int(np.prod([self.ncell[a] // self.box[a] for a in range(3)]))
+
+    # ------------------------------------------------------------------
+    def add_species(self, charge, mass, x, y, z, ux, uy, uz, w, ids=None) -> int:
+        arrs = [x, y, z, ux, uy, uz, w]
+        n = len(x)
+        keep = []
+        ptrs = (ctypes.c_void_p * 7)()
+        on_dev = 0
+        for i, a in enumerate(arrs):
+            if a is None:
+                ptrs[i] = None
+                continue
+            p, dev, k = _ptr(a if type(a).__module__.startswith("torch") else np.asarray(a, np.float64))
+            ptrs[i] = p
+            on_dev = dev
+            keep.append(k)
+        idp = None
+        if ids is not None:
+            idp, _, k = _ptr(ids if type(ids).__module__.startswith("torch") else np.asarray(ids, np.int64))
+            keep.append(k)
+        out = ctypes.c_int()
+        self._check(self._lib.pic_add_species(self._h, float(charge), float(mass), int(n), ptrs, idp,
+                                              on_dev, ctypes.byref(out)))
+        self.nspecies += 1
+        return out.value
+
+    def add_background(self, rho0):
+        self._check(self._lib.pic_add_background(self._h, float(rho0)))
+
+    def add_laser(self, a0, w0, tau, t_peak, omega, xc, yc, k_ant):
+        ld = L.LaserDesc(a0, w0, tau, t_peak, omega, xc, yc, int(k_ant))
+        self._check(self._lib.pic_add_laser(self._h, ctypes.byref(ld)))
+
+    def set_field(self, comp, data):
+        p, dev, k = _ptr(data if type(data).__module__.startswith("torch") else np.asarray(data, np.float64))
+        self._check(self._lib.pic_set_field(self._h, int(comp), p, dev))
+
+    def set_lb_params(self, **kw):
+        self._check(self._lib.pic_set_lb_params(self._h, ctypes.byref(lb_params(**kw))))
+
+    def step(self, nsteps=1):
+        self._check(self._lib.pic_step(self._h, int(nsteps)))
+
+    def sync(self):
+        self._check(self._lib.pic_sync(self._h))
+
+    def box_costs(self, strategy=L.COST_DEVICE_CLOCK):
+        c = np.empty(self.nboxes, np.float64)
+        n = np.empty(self.nboxes, np.int64)
+        self._check(self._lib.pic_get_box_costs(self._h, int(strategy), c.ctypes.data_as(L._pd),
+                                                n.ctypes.data_as(L._pi64)))
+        return c, n
+
+    def rebalance(self, **kw):
+        r = L.LBResult()
+        a = np.empty(self.nboxes, np.int32)
+        self._check(self._lib.pic_rebalance(self._h, ctypes.byref(lb_params(**kw)), ctypes.byref(r),
+                                            a.ctypes.data_as(L._pi32)))
+        return {"e_old": r.e_old, "e_new": r.e_new, "adopted": bool(r.adopted), "n_units": r.n_units,
+                "predicted_speedup": r.predicted_speedup, "assign": a}
+
+    def read_field(self, comp, out=None):
+        if out is None:
+            out = np.empty(self.ncells_total, np.float64)
+            self._check(self._lib.pic_read_fields(self._h, int(comp), ctypes.c_void_p(out.ctypes.data), 0))
+            return out.reshape(self.ncell[2], self.ncell[1], self.ncell[0])
+        p, dev, _ = _ptr(out)
+        self._check(self._lib.pic_read_fields(self._h, int(comp), p, dev))
+        return out
+
+    def num_particles(self, species=0) -> int:
+        n = ctypes.c_int64()
+        self._check(self._lib.pic_num_particles(self._h, int(species), ctypes.byref(n)))
+        return n.value
+
+    def particles(self, species=0) -> dict:
+        n = self.num_particles(species)
+        names = ("x", "y", "z", "ux", "uy", "uz", "w")
+        out = {k: np.empty(n, np.float64) for k in names}
+        ids = np.empty(n, np.int64)
+        ptrs = (ctypes.c_void_p * 7)(*[ctypes.c_void_p(out[k].ctypes.data) for k in names])
+        self._check(self._lib.pic_read_particles(self._h, int(species), ptrs, ctypes.c_void_p(ids.ctypes.data), 0))
+        out["id"] = ids
+        return out
+
+    def set_launch(self, threads=0, ctas_per_sm=0, split=0):
+        c = L.LaunchCfg(int(threads), int(ctas_per_sm), int(split))
+        self._check(self._lib.pic_set_launch(self._h, ctypes.byref(c)))
+
+    def get_launch(self):
+        c = L.LaunchCfg()
+        self._check(self._lib.pic_get_launch(self._h, ctypes.byref(c)))
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split}
+
+    def autotune(self, steps_per_candidate=2):
+        c = L.LaunchCfg()
+        self._check(self._lib.pic_autotune(self._h, int(steps_per_candidate), ctypes.byref(c)))
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split}
+
+    def set_profiling(self, on=True):
+        self._check(self._lib.pic_set_profiling(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = L.Stats()
+        self._check(self._lib.pic_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.Stats._fields_}
+
+
+def lb_params(mode=L.LB_DYNAMIC, interval=10, theta=0.10, policy=L.POLICY_KNAPSACK,
+              cost=L.COST_DEVICE_CLOCK, w_p=0.75, w_c=0.25, cap_factor=1.5, n_workers=0, split=0,
+              sched=L.SCHED_LISTS) -> L.LBParams:
+    return L.LBParams(int(mode), int(interval), float(theta), int(policy), int(cost), float(w_p),
+                      float(w_c), float(cap_factor), int(n_workers), int(split), int(sched))
+
+
+def balance_compute(costs, box_ijk, dim, n_workers, policy=L.POLICY_KNAPSACK, cap_factor=1.5):
+    """pic_balance_compute: the pure host balancer (no GPU needed)."""
+    lib = L.load()
+    c = np.ascontiguousarray(costs, np.float64)
+    ijk = None if box_ijk is None else np.ascontiguousarray(box_ijk, np.int32).reshape(-1)
+    out = np.empty(c.size, np.int32)
+    e = ctypes.c_double()
+    L.check(lib.pic_balance_compute(c.ctypes.data_as(L._pd), c.size,
+                                    None if ijk is None else ijk.ctypes.data_as(L._pi32), int(dim),
+                                    int(n_workers), int(policy), float(cap_factor),
+                                    out.ctypes.data_as(L._pi32), ctypes.byref(e)))
+    return out, e.value
+
+
+def lb_efficiency(costs, assign, n_workers) -> float:
+    lib = L.load()
+    c = np.ascontiguousarray(costs, np.float64)
+    a = np.ascontiguousarray(assign, np.int32)
+    e = ctypes.c_double()
+    L.check(lib.pic_lb_efficiency(c.ctypes.data_as(L._pd), a.ctypes.data_as(L._pi32), c.size,
+                                  int(n_workers), ctypes.byref(e)))
+    return e.value

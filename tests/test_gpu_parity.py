@@ -1,0 +1,198 @@
+"""GPU (libpic, through the C ABI) against the FP64 CPU oracle on identical
+seeded inputs.  Fields are compared element by element and particles matched by
+id; the bar is 1e-10 relative (max-norm, per array), since only the order of
+the atomic current sums differs.  Boxes, tiles and particle counts are chosen
+to span several tiles, ragged box counts, cell-crossing particles, both shape
+orders, both dimensionalities, the absorbing boundary with the laser antenna,
+and every scheduling mode."""
+import numpy as np
+import pytest
+
+import oracle as orc
+import paper_2104_11385_gb300 as pic
+from paper_2104_11385_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def make_oracle(wl, fields=None):
+    ref = orc.OracleSim(wl["dim"], wl["ncell"], wl["dx"], wl["dt"], wl["order"], wl.get("absorb", 0))
+    for sp in wl["species"]:
+        ref.add_species(sp["q"], sp["m"], sp["x"], sp["y"], sp["z"], sp["ux"], sp["uy"], sp["uz"],
+                        sp["w"], sp["id"])
+    if wl.get("laser"):
+        L = wl["laser"]
+        ref.set_laser(L["a0"], L["w0"], L["tau"], L["t_peak"], L["omega"], L["xc"], L["yc"], L["k_ant"])
+    if fields is not None:
+        for c, f in enumerate(fields):
+            ref.set_field(c, f)
+    return ref
+
+
+def make_gpu(wl, fields=None):
+    sim = pic.from_workload(wl)
+    if fields is not None:
+        for c, f in enumerate(fields):
+            sim.set_field(c, f)
+    return sim
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) if b.size else 0.0
+
+
+def compare(sim, ref, wl, tol=TOL, comps=range(9)):
+    sim.sync()
+    worst = {}
+    for c in comps:
+        worst[f"F{c}"] = rel(sim.read_field(c).reshape(-1), ref.field(c).reshape(-1))
+    L = [wl["ncell"][a] * wl["dx"][a] for a in range(3)]
+    for s in range(len(wl["species"])):
+        g, r = sim.particles(s), ref.particles(s)
+        assert g["id"].size == r["id"].size, f"species {s}: {g['id'].size} vs {r['id'].size} particles"
+        gi, ri = np.argsort(g["id"]), np.argsort(r["id"])
+        assert np.array_equal(g["id"][gi], r["id"][ri])
+        for a, k in enumerate(("x", "y", "z")):
+            if wl["dim"] == 2 and k == "y":
+                continue
+            d = np.abs(g[k][gi] - r[k][ri])
+            d = np.minimum(d, L[a] - d)  # periodic images
+            worst[f"s{s}{k}"] = float(d.max() / L[a]) if d.size else 0.0
+        for k in ("ux", "uy", "uz", "w"):
+            worst[f"s{s}{k}"] = rel(g[k][gi], r[k][ri])
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    assert not bad, f"parity above {tol}: {bad}"
+    return worst
+
+
+CASES = [
+    # dim, ncell, box, dx, order
+    (3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1),
+    (3, (24, 16, 16), (8, 8, 16), (0.3, 0.35, 0.4), 2),
+    (3, (16, 24, 32), (16, 8, 16), (0.25, 0.3, 0.3), 1),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.35), 1),
+    (2, (32, 1, 64), (32, 1, 32), (0.3, 1.0, 0.3), 2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d_o{c[4]}_{c[1][0]}x{c[1][1]}x{c[1][2]}" for c in CASES])
+def test_random_plasma_parity(case):
+    dim, n, box, dx, order = case
+    wl = workloads.random_plasma(100 + sum(n) + order, dim, n, box, dx, order, nspecies=2, npart=4000,
+                                 umax=2.0)
+    fields = workloads.random_fields(7, n, amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+
+
+def test_uniform32_full_size_parity():
+    wl = workloads.uniform32()
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_absorbing_boundary_and_laser_parity(dim):
+    if dim == 3:
+        n, box, dx = (16, 16, 48), (8, 8, 16), (0.3, 0.3, 0.3)
+    else:
+        n, box, dx = (32, 1, 64), (16, 1, 16), (0.3, 1.0, 0.3)
+    wl = workloads.random_plasma(300 + dim, dim, n, box, dx, 1, nspecies=2, npart=3000, umax=3.0,
+                                 absorb=6, laser=True)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.step(12)
+    ref.step(12)
+    compare(sim, ref, wl)
+    # some particles did leave through the absorbing layers
+    assert sim.num_particles(0) < 3000
+
+
+def test_lognormal_uneven_boxes_parity_with_balancing():
+    wl = workloads.lognormal(seed=5, nbox=(4, 4, 4), box=8, median=1500.0, sigma=1.0, order=2)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_lb_params(mode=pic.LB_DYNAMIC, interval=3, theta=0.0, split=8)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+
+
+@pytest.mark.parametrize("sched,policy,cost", [
+    (pic.SCHED_LISTS, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
+    (pic.SCHED_QUEUE, pic.POLICY_KNAPSACK, pic.COST_HEURISTIC),
+    (pic.SCHED_LISTS, pic.POLICY_SFC, pic.COST_HEURISTIC),
+])
+def test_schedule_does_not_change_physics(sched, policy, cost):
+    wl = workloads.random_plasma(77, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1, nspecies=1,
+                                 npart=6000, umax=1.0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_lb_params(mode=pic.LB_DYNAMIC, interval=2, theta=0.0, policy=policy, cost=cost, sched=sched,
+                      split=16)
+    sim.step(8)
+    ref.step(8)
+    compare(sim, ref, wl)
+
+
+@pytest.mark.parametrize("threads,cps", [(128, 1), (256, 2)])
+def test_launch_configuration_does_not_change_physics(threads, cps):
+    wl = workloads.random_plasma(78, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=1,
+                                 npart=5000, umax=1.0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(threads=threads, ctas_per_sm=cps)
+    sim.step(6)
+    ref.step(6)
+    compare(sim, ref, wl)
+
+
+def test_box_counts_and_clock_costs():
+    wl = workloads.lognormal(seed=9, nbox=(4, 4, 4), box=8, median=100.0, sigma=1.5, order=1)
+    sim = make_gpu(wl)
+    ref = make_oracle(wl)
+    sim.step(3)
+    ref.step(3)
+    clk, np_gpu = sim.box_costs(pic.COST_DEVICE_CLOCK)
+    heur, _ = sim.box_costs(pic.COST_HEURISTIC)
+    assert np.array_equal(np_gpu, ref.box_counts(wl["box"]))
+    assert np.all(clk[np_gpu > 0] > 0)
+    nc = np.prod(wl["box"])
+    np.testing.assert_allclose(heur, 0.75 * np_gpu + 0.25 * nc)
+    # clock cost tracks the particle count (Sec. 3.2: the schemes are consistent)
+    from scipy.stats import spearmanr
+    rho = spearmanr(clk, np_gpu).correlation
+    assert rho > 0.9, rho
+
+
+def test_empty_species_and_empty_run():
+    wl = workloads.random_plasma(5, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1, nspecies=1, npart=0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    fields = workloads.random_fields(3, (16, 16, 16), amp=0.1)
+    for c, f in enumerate(fields):
+        sim.set_field(c, f)
+        ref.set_field(c, f)
+    sim.step(5)
+    ref.step(5)
+    compare(sim, ref, wl)
+    assert sim.num_particles(0) == 0
+
+
+def test_rho_and_gauss_on_gpu():
+    wl = workloads.random_plasma(12, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=2,
+                                 npart=3000, umax=1.0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    assert rel(sim.read_field(pic.RHO).reshape(-1), ref.rho().reshape(-1)) < TOL
+    dx = wl["dx"]
+
+    def gauss(s):
+        Ex, Ey, Ez = (s.read_field(c) for c in (pic.EX, pic.EY, pic.EZ))
+        div = ((Ex - np.roll(Ex, 1, 2)) / dx[0] + (Ey - np.roll(Ey, 1, 1)) / dx[1]
+               + (Ez - np.roll(Ez, 1, 0)) / dx[2])
+        return div - s.read_field(pic.RHO)
+
+    r0 = gauss(sim)
+    scale = np.abs(sim.read_field(pic.RHO)).max()
+    sim.step(6)
+    assert np.abs(gauss(sim) - r0).max() < 1e-12 * scale

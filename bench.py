@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 PIC step with in-situ cost measurement and dynamic
+load balancing (the method of arXiv 2104.11385) on the 3D laser-foil workload:
+256^3 cells in 512 boxes of 32^3, a hydrogen foil 8 cells thick at 30 n_c with
+64 electrons + 64 protons per foil cell (67.1M particles), a0 = 20 laser, FP64.
+
+One step = one full PIC cycle (per-tile sort, TMA tile staging, gather, Boris
+push, Esirkepov deposit with clock64 box costs, Yee update, boundaries) plus
+the load-balancing routine every 10 steps (dynamic, knapsack, device-clock
+costs, threshold 10 %).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (weak
+scaling, no data-path collective); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6800.0
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# algorithmic FP64 flops per particle update (3D, linear shape): gather 141,
+# Boris push + position 80, Esirkepov weights and currents 213, current adds 54
+FLOPS_PER_PARTICLE = {(3, 1): 488.0, (3, 2): 1090.0, (2, 1): 230.0, (2, 2): 420.0}
+BYTES_PER_PARTICLE = 104.0  # read x,y,z,ux,uy,uz,w (56) + write x..uz (48)
+BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="foil256", choices=["foil256", "uniform32", "lognormal4096"])
+    ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (debug only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, scale, seed_offset=0):
+    from paper_2104_11385_gb300 import workloads as W
+    if name == "foil256":
+        return W.foil256(seed=2 + seed_offset, scale=scale)
+    if name == "uniform32":
+        return W.uniform32(seed=1 + seed_offset)
+    return W.lognormal(seed=3 + seed_offset)
+
+
+def workload_desc(wl):
+    nparts = sum(len(s["x"]) for s in wl["species"])
+    return {
+        "workload": wl["name"], "cells": list(wl["ncell"]), "box": list(wl["box"]),
+        "boxes": int(math.prod(wl["ncell"][a] // wl["box"][a] for a in range(3))),
+        "particles": nparts, "species": len(wl["species"]), "shape_order": wl["order"],
+        "lb": "dynamic knapsack, device-clock costs, interval 10, theta 0.10",
+        "l2": "inputs larger than L2 (particle state %.1f GB)" % (nparts * 64 / 1e9),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2104_11385_gb300 as pic
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    wl = make_workload(args.workload, args.scale, seed_offset=rank)
+    nparts = sum(len(s["x"]) for s in wl["species"])
+    ncells = int(math.prod(wl["ncell"]))
+    stream = torch.cuda.Stream()
+    lbkw = dict(mode=pic.LB_DYNAMIC, interval=10, theta=0.10, policy=pic.POLICY_KNAPSACK,
+                cost=pic.COST_DEVICE_CLOCK, sched=pic.SCHED_LISTS)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(sim, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- balanced (the paper's dynamic load balancing, on the SMs)
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    sim.step(1)                                      # measure per-box clock costs once
+    sim.rebalance(**dict(lbkw, theta=0.0))           # initial cost-driven mapping
+    sim.set_lb_params(**lbkw)
+    sim.step(args.warmup)
+    with ClockSampler(dev) as cs:
+        ms_bal = timed(sim, args.steps)
+    clocks = cs.summary()
+    # kernel-level timing (CUDA events on the library's stream around each launch)
+    sim.set_profiling(True)
+    sim.step(min(args.steps, 10))
+    st = sim.stats()
+    sim.set_profiling(False)
+    lb = sim.rebalance(**lbkw)
+    kernels_per_step = st["launches"] / max(st["steps"], 1)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- static box order (no load balancing: the fixed starting mapping)
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    sim.step(1 + args.warmup)
+    ms_static = timed(sim, args.steps)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for s in wl["species"]:
+            pinned.append({k: torch.from_numpy(np.ascontiguousarray(s[k])).pin_memory()
+                           for k in ("x", "y", "z", "ux", "uy", "uz", "w", "id")})
+        out_e = torch.empty(ncells, dtype=torch.float64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for p in pinned for v in p.values())
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = pic.Simulation(wl["dim"], wl["ncell"], wl["box"], wl["dx"], dt=wl["dt"],
+                             shape_order=wl["order"], absorb_cells=wl["absorb"], stream=stream.cuda_stream)
+        for s, p in zip(wl["species"], pinned):
+            sim.add_species(s["q"], s["m"], p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"], p["w"], ids=p["id"])
+        L = wl["laser"]
+        sim.add_laser(L["a0"], L["w0"], L["tau"], L["t_peak"], L["omega"], L["xc"], L["yc"], L["k_ant"])
+        sim.step(1)
+        sim.rebalance(**dict(lbkw, theta=0.0))
+        sim.set_lb_params(**lbkw)
+        sim.step(args.steps)
+        sim.read_field(pic.EX, out=out_e)
+        costs, npb = sim.box_costs(pic.COST_DEVICE_CLOCK)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d2h = out_e.numel() * 8 + costs.nbytes + npb.nbytes
+        sim.close()
+        secs = t1 - t0
+        if world > 1:
+            t = torch.tensor([secs], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            secs = float(t.item())
+        e2e = {"value": nparts * (args.steps + 1) * world / secs, "unit": "particle-updates/s",
+               "h2d_bytes_per_step": int(h2d / (args.steps + 1)),
+               "d2h_bytes_per_step": int(d2h / (args.steps + 1)),
+               "what": "pic_init + pic_add_species from pinned host arrays + 1 step + rebalance + K steps "
+                       "+ Ex and box costs back to the host"}
+
+    value = nparts * args.steps * world / (ms_bal / 1e3)
+    static_value = nparts * args.steps * world / (ms_static / 1e3)
+    ms_part = st["ms_particle"] / max(st["steps"], 1)
+    flops = FLOPS_PER_PARTICLE[(wl["dim"], wl["order"])] * nparts
+    achieved_tf = flops / (ms_part / 1e3) / 1e12
+    hbm = HBM_FALLBACK_GBS
+    peak_src = "fallback"
+    try:
+        hbm = float(json.load(open(MEASURED))["hbm_gbs"])
+        peak_src = "measured"
+    except Exception:
+        pass
+    hbm_achieved = BYTES_PER_PARTICLE * nparts / (ms_part / 1e3) / 1e9
+    return {
+        "value": value, "ms_per_step": ms_bal / args.steps, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": int(round(kernels_per_step * args.steps)),
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "pic_particle_kernel<3,1> (gather+Boris+Esirkepov+cost)",
+                     "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.19 TFLOP/s)",
+                     "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
+                             "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE}},
+        "static_order": {"value": static_value, "ms_per_step": ms_static / args.steps,
+                         "speedup_balanced_over_static": ms_static / ms_bal},
+        "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
+        "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
+                              "sort": st["ms_sort"] / max(st["steps"], 1)},
+        "fdtd_cell_updates_per_s": ncells / (st["ms_fields"] / max(st["steps"], 1) / 1e3),
+        "lb": {"e_old": lb["e_old"], "e_new": lb["e_new"], "n_units": lb["n_units"],
+               "predicted_speedup_sec4": lb["predicted_speedup"]},
+        "config": workload_desc(wl),
+    }
+
+
+def oracle_rate(wl_name, budget_s=15.0, steps=1):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the workload:
+    the same recipe at 1/4 of the extents (1/64 of the cells, the foil 2 cells
+    thick), timed over `steps` full PIC cycles on one host core."""
+    import oracle as orc
+    from paper_2104_11385_gb300 import workloads as W
+    if wl_name == "foil256":
+        wl = W.foil256(seed=2, scale=4)
+        sample = "foil256 recipe at 1/4 extents: 64^3 cells, foil 2 cells thick, %d particles, %d step(s)"
+    elif wl_name == "uniform32":
+        wl = W.uniform32(seed=1)
+        sample = "uniform32 in full: 32^3 cells, %d particles, %d step(s)"
+    else:
+        wl = W.lognormal(seed=3, nbox=(4, 4, 4))
+        sample = "lognormal recipe on 4^3 boxes of 16^3: %d particles, %d step(s)"
+    ref = orc.OracleSim(wl["dim"], wl["ncell"], wl["dx"], wl["dt"], wl["order"], wl["absorb"])
+    for s in wl["species"]:
+        ref.add_species(s["q"], s["m"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["id"])
+    if wl.get("laser"):
+        L = wl["laser"]
+        ref.set_laser(L["a0"], L["w0"], L["tau"], L["t_peak"], L["omega"], L["xc"], L["yc"], L["k_ant"])
+    nparts = sum(len(s["x"]) for s in wl["species"])
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        ref.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    secs = time.perf_counter() - t0
+    return nparts * done / secs, sample % (nparts, done), secs
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the reference arm is the FP64 CPU oracle, timed as it stands on the host cores
+        for _ in range(args.warmup):
+            oracle_rate(args.workload, budget_s=5.0, steps=1)
+        rates = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r, sample, _ = oracle_rate(args.workload, budget_s=5.0, steps=1)
+            rates.append(r)
+        secs = time.perf_counter() - t0
+        v = statistics.median(rates)
+        line = {"metric": "particle-updates/s", "value": v, "unit": "particle-updates/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload + " (bounded sample)", "sample": sample},
+                "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    res = run_ours(args, rank, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=6)
+        cpu = {"value": r, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+               "sample": sample + " (%.1f s of CPU time)" % secs}
+    if rank == 0:
+        line = {"metric": "particle-updates/s", "value": res["value"], "unit": "particle-updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded PCG64 workload recipe)",
+                "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
+                "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
+                "static_order": res["static_order"], "cell_updates_per_s": res["cell_updates_per_s"],
+                "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
+                "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

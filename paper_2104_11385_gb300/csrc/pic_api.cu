@@ -455,17 +455,15 @@ pic_status capture_graph(pic_sim* s) {
 
 pic_status configure_launch(pic_sim* s) {
     s->smem = pic_particle_smem_bytes(s->h.dim, s->h.order, s->h.T);
-    int per_sm = 0;
     cudaDeviceProp prop;
     CU(s, cudaGetDeviceProperties(&prop, s->device));
-    size_t smem_sm = prop.sharedMemPerMultiprocessor;
-    size_t need = s->smem + 1024 + 64;
-    int by_smem = (int)(smem_sm / need);
-    int by_threads = prop.maxThreadsPerMultiProcessor / s->threads;
-    per_sm = std::max(1, std::min({s->ctas_per_sm, by_smem, by_threads}));
     if (s->smem > prop.sharedMemPerBlockOptin)
         return fail(s, PIC_EUNSUPPORTED, "tile needs %zu bytes of shared memory", s->smem);
     CU(s, pic_prepare_particles(s->h.dim, s->h.order, s->smem));
+    // persistent grid: every CTA resident (registers, shared memory, threads)
+    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->threads, s->smem);
+    if (resident < 1) return fail(s, PIC_EUNSUPPORTED, "particle kernel does not fit on an SM");
+    int per_sm = std::max(1, std::min(s->ctas_per_sm, resident));
     s->ctas = s->nsm * per_sm;
     s->graph_dirty = true;
     return PIC_OK;

@@ -75,6 +75,57 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Exact floor and fractional part of x.  On GB300 every FP64 instruction,
+// conversions included, issues at the FP64 rate (about 2 per SM per clock), so
+// for 0 <= x < 2^31 both come from integer work on the IEEE-754 bits; other x
+// go through floor().  Both routes give the identical (exact) results.
+__device__ __forceinline__ int ifloor_frac(double x, double& f) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((unsigned long long)b >> 52) - 1023;  // sign set -> e > 1023
+    if (e < 0) {
+        if (b >= 0) {  // 0 <= x < 1
+            f = x;
+            return 0;
+        }
+    } else if (e < 31) {
+        const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        const int sh = 52 - e;
+        const int i = (int)(m >> sh);
+        const unsigned long long fm = m & ((1ull << sh) - 1ull);
+        if (fm == 0ull) {
+            f = 0.0;
+        } else {
+            const int top = 63 - __clzll((long long)fm);
+            const unsigned long long bits = ((unsigned long long)(top - sh + 1023) << 52) |
+                                            ((fm << (52 - top)) & 0xFFFFFFFFFFFFFull);
+            f = __longlong_as_double((long long)bits);
+        }
+        return i;
+    }
+    const double fl = floor(x);
+    f = x - fl;
+    return (int)fl;
+}
+
+// floor of x >= 0 (x < 2^31) by integer work; floor() otherwise
+__device__ __forceinline__ int ifloor(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((unsigned long long)b >> 52) - 1023;
+    if (e < 0 && b >= 0) return 0;
+    if (e >= 0 && e < 31)
+        return (int)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) >> (52 - e));
+    return (int)floor(x);
+}
+
+// x < 0 and x >= y for y > 0 by integer comparison of the bit patterns
+__device__ __forceinline__ bool is_neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool ge_pos(double x, double y) {
+    return __double_as_longlong(x) >= __double_as_longlong(y);
+}
+__device__ __forceinline__ bool ge_half(double f) {  // f >= 0.5 for f >= 0
+    return __double_as_longlong(f) >= 0x3FE0000000000000ll;
+}
+
 // one-dimensional B-spline support: first node and ORDER+1 weights
 template <int ORDER>
 struct Support {
@@ -82,24 +133,58 @@ struct Support {
     double w[ORDER + 1];
 };
 
+// support of a node-centred quantity at xi (cells, from the tile origin)
 template <int ORDER>
 __device__ __forceinline__ Support<ORDER> support(double xi) {
     Support<ORDER> r;
+    double f;
+    const int i = ifloor_frac(xi, f);
     if (ORDER == 1) {
-        r.s = __double2int_rd(xi);
-        double f = xi - (double)r.s;
+        r.s = i;
         r.w[0] = 1.0 - f;
         r.w[1] = f;
     } else {
-        int c = __double2int_rd(xi + 0.5);
-        double d = xi - (double)c;  // in [-1/2, 1/2)
-        double a = 0.5 - d, b = 0.5 + d;
-        r.s = c - 1;
-        r.w[0] = 0.5 * a * a;
-        r.w[1] = 0.75 - d * d;
-        r.w[ORDER] = 0.5 * b * b;
+        // nearest node c = floor(xi + 1/2), d = xi - c in [-1/2, 1/2)
+        const bool up = ge_half(f);
+        const double d = up ? f - 1.0 : f;
+        const double a = 0.5 - d, b = 0.5 + d;
+        r.s = i + (up ? 1 : 0) - 1;
+        r.w[0] = 0.5 * (a * a);
+        r.w[1] = fma(-d, d, 0.75);
+        r.w[ORDER] = 0.5 * (b * b);
     }
     return r;
+}
+
+// node and half-node supports of one position (the half-node grid is shifted
+// by +1/2 cell: Ex along x, etc.)
+template <int ORDER>
+__device__ __forceinline__ void supports(double xi, Support<ORDER>& nd, Support<ORDER>& hf) {
+    double f;
+    const int i = ifloor_frac(xi, f);
+    const bool up = ge_half(f);
+    if (ORDER == 1) {
+        nd.s = i;
+        nd.w[0] = 1.0 - f;
+        nd.w[1] = f;
+        const double g = f + (up ? -0.5 : 0.5);  // xi - 1/2 - floor(xi - 1/2)
+        hf.s = up ? i : i - 1;
+        hf.w[0] = 1.0 - g;
+        hf.w[1] = g;
+    } else {
+        const double d = up ? f - 1.0 : f;  // node: xi - floor(xi + 1/2)
+        const double a = 0.5 - d, b = 0.5 + d;
+        nd.s = i + (up ? 1 : 0) - 1;
+        nd.w[0] = 0.5 * (a * a);
+        nd.w[1] = fma(-d, d, 0.75);
+        nd.w[ORDER] = 0.5 * (b * b);
+        const double h = f - 0.5;  // half: (xi - 1/2) - floor(xi), nearest half-node floor(xi)
+        const double ah = 0.5 - h, bh = 0.5 + h;
+        hf.s = i - 1;
+        hf.w[0] = 0.5 * (ah * ah);
+        hf.w[1] = fma(-h, h, 0.75);
+        hf.w[ORDER] = 0.5 * (bh * bh);
+    }
 }
 
 // interpolation of one component from a shared tile with extents (SX, SY)
@@ -138,22 +223,22 @@ __device__ __forceinline__ double interp(const double* __restrict__ F, int SX, i
     }
 }
 
-// Esirkepov node shapes on the common window of W = ORDER + 2 nodes that
-// starts at the lower of the two supports.
-template <int ORDER>
+// Esirkepov node shapes on a common window of W nodes starting at the lower of
+// the two supports: W = ORDER + 1 when the particle keeps its support (the
+// in-cell case, most particles), W = ORDER + 2 when it moves to a neighbour.
+template <int ORDER, int W>
 struct Window {
     int base;
-    double S0[ORDER + 2];
-    double DS[ORDER + 2];
+    double S0[W];
+    double DS[W];
 };
 
-template <int ORDER>
+template <int ORDER, int W>
 __device__ __forceinline__ bool make_window(const Support<ORDER>& a, const Support<ORDER>& b,
-                                            Window<ORDER>& win) {
-    constexpr int W = ORDER + 2;
+                                            Window<ORDER, W>& win) {
     int base = min(a.s, b.s);
-    int oa = a.s - base, ob = b.s - base;  // 0 or 1 when the move is below one cell
-    if ((oa | ob) & ~1) return false;
+    int oa = a.s - base, ob = b.s - base;
+    if (oa > W - ORDER - 1 || ob > W - ORDER - 1) return false;
     win.base = base;
 #pragma unroll
     for (int l = 0; l < W; ++l) {
@@ -203,7 +288,11 @@ __device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
     if (lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
 }
 
-// Shared-memory layout sizes for a tile configuration
+// Shared-memory layout: six E/B tiles (TMA destinations), three J tiles, and
+// the queue of cell-crossing particles (struct of arrays, QCAP slots).
+constexpr int QCAP = 512;
+constexpr int QF = 8;  // queue fields: xl yl zl dX dY dZ qw vy
+
 struct SmemPlan {
     int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
     int j_stride;   // doubles per J component
@@ -216,8 +305,8 @@ __host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3])
     p.eb_vol = ebs[0] * ebs[1] * ebs[2];
     p.j_vol = js[0] * js[1] * js[2];
     p.eb_stride = (p.eb_vol + 15) & ~15;
-    p.j_stride = p.j_vol;
-    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);
+    p.j_stride = (p.j_vol + 1) & ~1;
+    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride + QF * QCAP) * sizeof(double);
     return p;
 }
 
@@ -237,11 +326,135 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restric
     }
 }
 
+// Esirkepov deposit of one particle into the shared J tile on windows of W
+// nodes per direction.  n: node supports at x^n, m: at x^{n+1} (local cells).
+// Prefix sums of DS along each current's own direction times the transverse
+// weight A_a S0_b + C_a DS_b with A = S0 + DS/2, C = S0/2 + DS/3.
+template <int DIM, int ORDER, int W>
+__device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ, const SmemPlan& P,
+                                        double qw, double vy, const Support<ORDER>& n0,
+                                        const Support<ORDER>& n1, const Support<ORDER>& n2,
+                                        const Support<ORDER>& m0, const Support<ORDER>& m1,
+                                        const Support<ORDER>& m2) {
+    Window<ORDER, W> wx, wy, wz;
+    bool ok = make_window<ORDER, W>(n0, m0, wx) && make_window<ORDER, W>(n2, m2, wz);
+    if (DIM == 3) ok = ok && make_window<ORDER, W>(n1, m1, wy);
+    if (!ok) return false;
+    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    double* Jx = sJ;
+    double* Jy = sJ + P.j_stride;
+    double* Jz = sJ + 2 * P.j_stride;
+    double Ax[W], Cx[W], Az[W];
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        Ax[l] = fma(0.5, wx.DS[l], wx.S0[l]);
+        Cx[l] = fma(kThird, wx.DS[l], 0.5 * wx.S0[l]);
+        Az[l] = fma(0.5, wz.DS[l], wz.S0[l]);
+    }
+    if (DIM == 3) {
+        double Ay[W], Cy[W];
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            Ay[l] = fma(0.5, wy.DS[l], wy.S0[l]);
+            Cy[l] = fma(kThird, wy.DS[l], 0.5 * wy.S0[l]);
+        }
+        const int bx = wx.base + lo, by = wy.base + lo, bz = wz.base + lo;
+        {
+            const double c = qw * S.jfac[0];
+            double Pf[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; Pf[l] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    double T = fma(Ay[j], wz.S0[k], Cy[j] * wz.DS[k]);
+                    double* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
+#pragma unroll
+                    for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, Pf[l] * T);
+                }
+        }
+        {
+            const double c = qw * S.jfac[1];
+            double Pf[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < W - 1; ++j) { acc += wy.DS[j]; Pf[j] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    double T = fma(Ax[i], wz.S0[k], Cx[i] * wz.DS[k]);
+                    double* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
+#pragma unroll
+                    for (int j = 0; j < W - 1; ++j) atomicAdd(col + j * jx, Pf[j] * T);
+                }
+        }
+        {
+            const double c = qw * S.jfac[2];
+            double Pf[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) { acc += wz.DS[k]; Pf[k] = c * acc; }
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    double T = fma(Ax[i], wy.S0[j], Cx[i] * wy.DS[j]);
+                    double* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
+#pragma unroll
+                    for (int k = 0; k < W - 1; ++k) atomicAdd(col + k * jx * jy, Pf[k] * T);
+                }
+        }
+    } else {
+        const int bx = wx.base + lo, bz = wz.base + lo;
+        {  // Jx(i,k) = -(q w /(dz dt)) sum_{i'<=i} DSx(i') (S0z + DSz/2)
+            const double c = qw * S.jfac[0];
+            double Pf[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; Pf[l] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                double* row = Jx + (bz + k) * jx + bx;
+#pragma unroll
+                for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, Pf[l] * Az[k]);
+            }
+        }
+        {
+            const double c = qw * S.jfac[2];
+            double Pf[W - 1];
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) { acc += wz.DS[k]; Pf[k] = c * acc; }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                double* col = Jz + bz * jx + (bx + i);
+#pragma unroll
+                for (int k = 0; k < W - 1; ++k) atomicAdd(col + k * jx, Pf[k] * Ax[i]);
+            }
+        }
+        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax S0z + Cx DSz)
+            const double c = qw * vy * S.jyfac2d;
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    atomicAdd(Jy + (bz + k) * jx + (bx + i), c * fma(Ax[i], wz.S0[k], Cx[i] * wz.DS[k]));
+        }
+    }
+    return true;
+}
+
+// Gather, Boris push, and deposit of one particle.  Particles that keep their
+// support in every direction deposit at once on the small window; the others
+// go to the shared queue, drained in full warps by drain_queue.
 template <int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
                                          const double* __restrict__ sEB, double* __restrict__ sJ,
-                                         const SmemPlan& P, int64_t p, int32_t* err) {
-    constexpr int W = ORDER + 2;
+                                         double* __restrict__ sQ, int* s_qn, const SmemPlan& P,
+                                         int64_t p, int32_t* err) {
     double X = sp.cur[0][p], Z = sp.cur[2][p];
     double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
     double u0 = sp.cur[3][p], u1 = sp.cur[4][p], u2 = sp.cur[5][p];
@@ -252,15 +465,15 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     const double zl = Z - (double)tl.o[2];
 
     // ---- gather at x^n: node and half-node supports per direction
-    Support<ORDER> nx = support<ORDER>(xl), hx = support<ORDER>(xl - 0.5);
-    Support<ORDER> nz = support<ORDER>(zl), hz = support<ORDER>(zl - 0.5);
-    Support<ORDER> ny, hy;
+    Support<ORDER> nd[3], hf[3];
+    supports<ORDER>(xl, nd[0], hf[0]);
+    supports<ORDER>(zl, nd[2], hf[2]);
     if (DIM == 3) {
-        ny = support<ORDER>(yl);
-        hy = support<ORDER>(yl - 0.5);
+        supports<ORDER>(yl, nd[1], hf[1]);
     } else {
-        ny.s = -1; ny.w[0] = 1.0;
-        hy = ny;
+        nd[1].s = -1;
+        nd[1].w[0] = 1.0;
+        hf[1] = nd[1];
     }
     {
         // the particle must sit in its tile (local cell index in [0, T)):
@@ -268,11 +481,11 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         // support start = floor(xl) - 1
         bool in;
         if (ORDER == 1) {
-            in = nx.s >= 0 && nx.s < S.T[0] && nz.s >= 0 && nz.s < S.T[2];
-            if (DIM == 3) in = in && ny.s >= 0 && ny.s < S.T[1];
+            in = nd[0].s >= 0 && nd[0].s < S.T[0] && nd[2].s >= 0 && nd[2].s < S.T[2];
+            if (DIM == 3) in = in && nd[1].s >= 0 && nd[1].s < S.T[1];
         } else {
-            in = hx.s >= -1 && hx.s < S.T[0] - 1 && hz.s >= -1 && hz.s < S.T[2] - 1;
-            if (DIM == 3) in = in && hy.s >= -1 && hy.s < S.T[1] - 1;
+            in = hf[0].s >= -1 && hf[0].s < S.T[0] - 1 && hf[2].s >= -1 && hf[2].s < S.T[2] - 1;
+            if (DIM == 3) in = in && hf[1].s >= -1 && hf[1].s < S.T[1] - 1;
         }
         if (!in) {
             atomicOr(err, PIC_DERR_BOUNDS);
@@ -288,12 +501,12 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     const double* Bx = sEB + 3 * P.eb_stride;
     const double* By = sEB + 4 * P.eb_stride;
     const double* Bz = sEB + 5 * P.eb_stride;
-    double e0 = interp<ORDER, DIM>(Ex, SX, SY, hx, ny, nz);
-    double e1 = interp<ORDER, DIM>(Ey, SX, SY, nx, hy, nz);
-    double e2 = interp<ORDER, DIM>(Ez, SX, SY, nx, ny, hz);
-    double b0 = interp<ORDER, DIM>(Bx, SX, SY, nx, hy, hz);
-    double b1 = interp<ORDER, DIM>(By, SX, SY, hx, ny, hz);
-    double b2 = interp<ORDER, DIM>(Bz, SX, SY, hx, hy, nz);
+    double e0 = interp<ORDER, DIM>(Ex, SX, SY, hf[0], nd[1], nd[2]);
+    double e1 = interp<ORDER, DIM>(Ey, SX, SY, nd[0], hf[1], nd[2]);
+    double e2 = interp<ORDER, DIM>(Ez, SX, SY, nd[0], nd[1], hf[2]);
+    double b0 = interp<ORDER, DIM>(Bx, SX, SY, nd[0], hf[1], hf[2]);
+    double b1 = interp<ORDER, DIM>(By, SX, SY, hf[0], nd[1], hf[2]);
+    double b2 = interp<ORDER, DIM>(Bz, SX, SY, hf[0], hf[1], nd[2]);
 
     // ---- relativistic Boris push
     const double k = sp.kq;
@@ -319,152 +532,55 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     double dY = (DIM == 3) ? v1 * S.dtd[1] : 0.0;
 
     // ---- Esirkepov deposit of J^{n+1/2} from x^n to x^{n+1}
-    const double x1l = xl + dX, z1l = zl + dZ;
-    Support<ORDER> mx = support<ORDER>(x1l), mz = support<ORDER>(z1l);
-    Window<ORDER> wx, wz, wy;
-    bool ok = make_window<ORDER>(nx, mx, wx) && make_window<ORDER>(nz, mz, wz);
-    if (DIM == 3) {
-        Support<ORDER> my = support<ORDER>(yl + dY);
-        ok = ok && make_window<ORDER>(ny, my, wy);
-    }
-    if (!ok) {
-        atomicOr(err, PIC_DERR_BOUNDS);
-        sp.key[p] = S.ntiles;
-        warp_hist_add(sp.count, S.ntiles);
-        return;
-    }
+    Support<ORDER> mv[3];
+    mv[0] = support<ORDER>(xl + dX);
+    mv[2] = support<ORDER>(zl + dZ);
+    if (DIM == 3) mv[1] = support<ORDER>(yl + dY);
+    else mv[1] = nd[1];
     const double qw = sp.q * w;
-    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
-    double* Jx = sJ;
-    double* Jy = sJ + P.j_stride;
-    double* Jz = sJ + 2 * P.j_stride;
-    double Ax[W], Cx[W], Az[W], Cz[W];
-#pragma unroll
-    for (int l = 0; l < W; ++l) {
-        Ax[l] = fma(0.5, wx.DS[l], wx.S0[l]);
-        Cx[l] = fma(kThird, wx.DS[l], 0.5 * wx.S0[l]);
-        Az[l] = fma(0.5, wz.DS[l], wz.S0[l]);
-        Cz[l] = fma(kThird, wz.DS[l], 0.5 * wz.S0[l]);
-    }
-    if (DIM == 3) {
-        double Ay[W], Cy[W];
-#pragma unroll
-        for (int l = 0; l < W; ++l) {
-            Ay[l] = fma(0.5, wy.DS[l], wy.S0[l]);
-            Cy[l] = fma(kThird, wy.DS[l], 0.5 * wy.S0[l]);
-        }
-        const int bx = wx.base + lo, by = wy.base + lo, bz = wz.base + lo;
-        // Jx: prefix sum along x of DSx, times the (y,z) weight
-        {
-            const double c = qw * S.jfac[0];
-            double P_[W - 1];
-            double acc = 0.0;
-#pragma unroll
-            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; P_[l] = c * acc; }
-#pragma unroll
-            for (int n = 0; n < W; ++n)
-#pragma unroll
-                for (int m = 0; m < W; ++m) {
-                    double T = fma(Ay[m], wz.S0[n], Cy[m] * wz.DS[n]);
-                    double* row = Jx + ((bz + n) * jy + (by + m)) * jx + bx;
-#pragma unroll
-                    for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, P_[l] * T);
-                }
-        }
-        {
-            const double c = qw * S.jfac[1];
-            double P_[W - 1];
-            double acc = 0.0;
-#pragma unroll
-            for (int m = 0; m < W - 1; ++m) { acc += wy.DS[m]; P_[m] = c * acc; }
-#pragma unroll
-            for (int n = 0; n < W; ++n)
-#pragma unroll
-                for (int l = 0; l < W; ++l) {
-                    double T = fma(Ax[l], wz.S0[n], Cx[l] * wz.DS[n]);
-                    double* col = Jy + ((bz + n) * jy + by) * jx + (bx + l);
-#pragma unroll
-                    for (int m = 0; m < W - 1; ++m) atomicAdd(col + m * jx, P_[m] * T);
-                }
-        }
-        {
-            const double c = qw * S.jfac[2];
-            double P_[W - 1];
-            double acc = 0.0;
-#pragma unroll
-            for (int n = 0; n < W - 1; ++n) { acc += wz.DS[n]; P_[n] = c * acc; }
-#pragma unroll
-            for (int m = 0; m < W; ++m)
-#pragma unroll
-                for (int l = 0; l < W; ++l) {
-                    double T = fma(Ax[l], wy.S0[m], Cx[l] * wy.DS[m]);
-                    double* col = Jz + (bz * jy + (by + m)) * jx + (bx + l);
-#pragma unroll
-                    for (int n = 0; n < W - 1; ++n) atomicAdd(col + n * jx * jy, P_[n] * T);
-                }
-        }
+    bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
+    if (same) {
+        deposit<DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
     } else {
-        const int bx = wx.base + lo, bz = wz.base + lo;
-        {  // Jx(l,n) = -(q w /(dz dt)) sum_{l'<=l} DSx(l') (S0z + DSz/2)
-            const double c = qw * S.jfac[0];
-            double P_[W - 1];
-            double acc = 0.0;
-#pragma unroll
-            for (int l = 0; l < W - 1; ++l) { acc += wx.DS[l]; P_[l] = c * acc; }
-#pragma unroll
-            for (int n = 0; n < W; ++n) {
-                double* row = Jx + (bz + n) * jx + bx;
-#pragma unroll
-                for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, P_[l] * Az[n]);
-            }
-        }
-        {
-            const double c = qw * S.jfac[2];
-            double P_[W - 1];
-            double acc = 0.0;
-#pragma unroll
-            for (int n = 0; n < W - 1; ++n) { acc += wz.DS[n]; P_[n] = c * acc; }
-#pragma unroll
-            for (int l = 0; l < W; ++l) {
-                double* col = Jz + bz * jx + (bx + l);
-#pragma unroll
-                for (int n = 0; n < W - 1; ++n) atomicAdd(col + n * jx, P_[n] * Ax[l]);
-            }
-        }
-        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax S0z + Cx DSz)
-            const double c = qw * v1 * S.jyfac2d;
-#pragma unroll
-            for (int n = 0; n < W; ++n)
-#pragma unroll
-                for (int l = 0; l < W; ++l)
-                    atomicAdd(Jy + (bz + n) * jx + (bx + l),
-                              c * fma(Ax[l], wz.S0[n], Cx[l] * wz.DS[n]));
+        int slot = atomicAdd(s_qn, 1);
+        if (slot < QCAP) {
+            sQ[0 * QCAP + slot] = xl;
+            sQ[1 * QCAP + slot] = yl;
+            sQ[2 * QCAP + slot] = zl;
+            sQ[3 * QCAP + slot] = dX;
+            sQ[4 * QCAP + slot] = dY;
+            sQ[5 * QCAP + slot] = dZ;
+            sQ[6 * QCAP + slot] = qw;
+            sQ[7 * QCAP + slot] = v1;
+        } else {
+            atomicOr(err, PIC_DERR_BOUNDS);  // cannot happen: the queue drains before it fills
         }
     }
 
     // ---- new position, boundary, re-sort key
+    const double nxd = (double)S.n[0], nyd = (double)S.n[1], nzd = (double)S.n[2];
     X += dX;
     Z += dZ;
-    if (X < 0.0) X += (double)S.n[0];
-    if (X >= (double)S.n[0]) X -= (double)S.n[0];
+    if (is_neg(X)) X += nxd;
+    if (ge_pos(X, nxd)) X -= nxd;
     if (DIM == 3) {
         Y += dY;
-        if (Y < 0.0) Y += (double)S.n[1];
-        if (Y >= (double)S.n[1]) Y -= (double)S.n[1];
+        if (is_neg(Y)) Y += nyd;
+        if (ge_pos(Y, nyd)) Y -= nyd;
     }
     int key;
     if (S.absorb > 0) {
         if (Z < (double)S.absorb || Z >= (double)(S.n[2] - S.absorb)) key = S.ntiles;
         else key = -1;
     } else {
-        if (Z < 0.0) Z += (double)S.n[2];
-        if (Z >= (double)S.n[2]) Z -= (double)S.n[2];
+        if (is_neg(Z)) Z += nzd;
+        if (ge_pos(Z, nzd)) Z -= nzd;
         key = -1;
     }
     if (key < 0) {
-        int ix = min(__double2int_rd(X), S.n[0] - 1);
-        int iy = (DIM == 3) ? min(__double2int_rd(Y), S.n[1] - 1) : 0;
-        int iz = min(__double2int_rd(Z), S.n[2] - 1);
+        int ix = min(max(ifloor(X), 0), S.n[0] - 1);
+        int iy = (DIM == 3) ? min(max(ifloor(Y), 0), S.n[1] - 1) : 0;
+        int iz = min(max(ifloor(Z), 0), S.n[2] - 1);
         key = tile_key(S, ix, iy, iz);
     }
     sp.cur[0][p] = X;
@@ -477,6 +593,34 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     warp_hist_add(sp.count, key);
 }
 
+// Deposits every queued (cell-crossing) particle on the ORDER + 2 window;
+// all threads of the CTA call it together.
+template <int DIM, int ORDER>
+__device__ void drain_queue(const SimDev& S, double* __restrict__ sJ, const double* __restrict__ sQ,
+                            int qn, const SmemPlan& P, int32_t* err) {
+    qn = min(qn, QCAP);
+    for (int i = threadIdx.x; i < qn; i += blockDim.x) {
+        const double xl = sQ[0 * QCAP + i], yl = sQ[1 * QCAP + i], zl = sQ[2 * QCAP + i];
+        const double dX = sQ[3 * QCAP + i], dY = sQ[4 * QCAP + i], dZ = sQ[5 * QCAP + i];
+        const double qw = sQ[6 * QCAP + i], vy = sQ[7 * QCAP + i];
+        Support<ORDER> nd[3], mv[3];
+        nd[0] = support<ORDER>(xl);
+        nd[2] = support<ORDER>(zl);
+        mv[0] = support<ORDER>(xl + dX);
+        mv[2] = support<ORDER>(zl + dZ);
+        if (DIM == 3) {
+            nd[1] = support<ORDER>(yl);
+            mv[1] = support<ORDER>(yl + dY);
+        } else {
+            nd[1].s = -1;
+            nd[1].w[0] = 1.0;
+            mv[1] = nd[1];
+        }
+        if (!deposit<DIM, ORDER, ORDER + 2>(S, sJ, P, qw, vy, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]))
+            atomicOr(err, PIC_DERR_BOUNDS);
+    }
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -486,14 +630,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }  // namespace
 
 template <int DIM, int ORDER>
-__global__ void __launch_bounds__(256) pic_particle_kernel(const SchedDev* __restrict__ sd,
+__global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                            SimDev* __restrict__ sims) {
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
     double* smem = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-    __shared__ int s_unit, s_list, s_abort;
+    __shared__ int s_unit, s_list, s_abort, s_qn;
     __shared__ unsigned long long s_cost;
 
     const int nlists = sd->meta[0];
@@ -503,6 +647,7 @@ __global__ void __launch_bounds__(256) pic_particle_kernel(const SchedDev* __res
         mbar_init(&bar);
         s_list = my_list;
         s_abort = 0;
+        s_qn = 0;
         s_cost = 0ull;
     }
     __syncthreads();
@@ -584,8 +729,21 @@ __global__ void __launch_bounds__(256) pic_particle_kernel(const SchedDev* __res
                     }
                 }
                 const unsigned long long c0 = clock64();
-                for (int64_t p = s0 + threadIdx.x; p < s1; p += blockDim.x)
-                    push_one<DIM, ORDER>(S, sp, cur, sEB, sJ, P, p, sd->err);
+                double* sQ = sJ + 3 * P.j_stride;
+                for (int64_t base = s0; base < s1; base += blockDim.x) {
+                    const int64_t p = base + threadIdx.x;
+                    if (p < s1) push_one<DIM, ORDER>(S, sp, cur, sEB, sJ, sQ, &s_qn, P, p, sd->err);
+                    __syncthreads();
+                    const int qn = s_qn;
+                    __syncthreads();
+                    // drain the crossing queue when it could overflow next round,
+                    // and always before the segment (and its tile) ends
+                    if (qn > 0 && (qn > QCAP - (int)blockDim.x || base + blockDim.x >= s1)) {
+                        drain_queue<DIM, ORDER>(S, sJ, sQ, qn, P, sd->err);
+                        if (threadIdx.x == 0) s_qn = 0;
+                        __syncthreads();
+                    }
+                }
                 my_clk += clock64() - c0;
             }
         }
@@ -756,6 +914,20 @@ static cudaError_t launch_particles_t(const LaunchCfg& cfg, size_t smem, const S
                                       SimDev* sims, cudaStream_t st) {
     pic_particle_kernel<DIM, ORDER><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
     return cudaGetLastError();
+}
+
+int pic_particle_occupancy(int dim, int order, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (dim == 3 && order == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<3, 1>, threads, smem);
+    else if (dim == 3 && order == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<3, 2>, threads, smem);
+    else if (dim == 2 && order == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<2, 1>, threads, smem);
+    else if (dim == 2 && order == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<2, 2>, threads, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {

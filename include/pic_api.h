@@ -90,7 +90,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out);
  * ignored in 2D (may be NULL).  ids: np int64 (NULL: 0..np-1).  All arrays are
  * host pointers (on_device = 0) or device pointers (on_device = 1); they are
  * copied.  Positions must lie in [0, L); with absorb_cells > 0, z must lie
- * outside the damping layers.  capacity_hint >= np reserves room (0: np).
+ * outside the damping layers.
  * *species_id_out receives the species index.  Errors: PIC_EINVAL,
  * PIC_ENOMEM, PIC_ECUDA, PIC_ESTATE (after the first pic_step). */
 pic_status pic_add_species(pic_sim* sim, double charge, double mass, int64_t np,
@@ -234,6 +234,24 @@ pic_status pic_num_particles(pic_sim* sim, int species, int64_t* np_out);
  * by box); match them by id.  Host or device buffers.  Synchronises. */
 pic_status pic_read_particles(pic_sim* sim, int species, double* const soa_out[7],
                               int64_t* id_out, int on_device);
+
+/* Bins caller-owned particles by box (Sec. 2.1: a box owns the particles
+ * inside it; Sec. 2.2 moves particles with their box when the mapping
+ * changes).  A particle's box is floor(x/dx) wrapped into [0, ncell) divided
+ * by the box extent, per direction; box index (bz*nby + by)*nbx + bx.
+ *   grid         geometry only: dim, ncell, box, dx; stream (NULL: legacy
+ *                default stream).  Other fields are ignored.
+ *   x, y, z      device, np doubles each (y unused and may be NULL in 2D).
+ *   np           0 <= np < 2^31.
+ *   box_off_out  device, nboxes+1 int64: exclusive prefix of the per-box
+ *                counts (box b holds perm_out[box_off_out[b] .. box_off_out[b+1])).
+ *   perm_out     device, np int64: particle indices grouped by box; the order
+ *                inside a box is unspecified.
+ * Asynchronous on the stream; per-box cursors are allocated stream-ordered
+ * (cudaMallocAsync) and freed before return.  Errors: PIC_EINVAL, PIC_ENOMEM,
+ * PIC_ECUDA (message in pic_last_error(NULL)). */
+pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const double* y,
+                             const double* z, int64_t np, int64_t* box_off_out, int64_t* perm_out);
 
 /* Launch configuration of the persistent particle kernel and the work
  * splitting (the autotuner's knobs).  Any field <= 0 keeps its value.

@@ -84,6 +84,7 @@ def lib():
             L.orc_morton.argtypes = [ctypes.c_int, _i64, _i64, _i64]
             L.orc_sfc.argtypes = [_pd, _pi32, _i64, ctypes.c_int, ctypes.c_int, _pi32]
             L.orc_lb_adopt.argtypes = [_d, _d, _d]
+            L.orc_bin_particles.argtypes = [ctypes.c_int, _pi64, _pd, _pi64, _pd, _pd, _pd, _i64, _pi64, _pi64]
             L.orc_predicted_speedup.restype = _d
             L.orc_predicted_speedup.argtypes = [_d, _d]
             _lib = L
@@ -222,6 +223,21 @@ def sfc(costs, box_ijk, dim, n_workers) -> np.ndarray:
                      out.ctypes.data_as(_pi32)) != 0:
         raise ValueError("bad sfc input")
     return out
+
+
+def bin_particles(dim, n, d, bsize, x, y, z):
+    """Stable binning of particles by box: (box_off[nboxes+1], perm[np])."""
+    xs, ys, zs = (_c64(a) for a in (x, y if y is not None else np.zeros(len(x)), z))
+    nb = int(np.prod([int(n[a]) // int(bsize[a]) for a in range(3)]))
+    off = np.zeros(nb + 1, np.int64)
+    perm = np.zeros(xs.size, np.int64)
+    na, ba = np.array(n, np.int64), np.array(bsize, np.int64)
+    da = np.array(d, np.float64)
+    if lib().orc_bin_particles(int(dim), na.ctypes.data_as(_pi64), _dp(da), ba.ctypes.data_as(_pi64),
+                               _dp(xs), _dp(ys), _dp(zs), xs.size, off.ctypes.data_as(_pi64),
+                               perm.ctypes.data_as(_pi64)) != 0:
+        raise ValueError("bad binning arguments")
+    return off, perm
 
 
 def lb_adopt(e_old, e_new, theta) -> bool:

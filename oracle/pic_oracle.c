@@ -550,6 +550,37 @@ int orc_box_counts(const orc_sim* s, const int64_t bsize[3], int64_t* counts) {
     return 0;
 }
 
+int orc_bin_particles(int dim, const int64_t n[3], const double d[3], const int64_t bsize[3],
+                      const double* x, const double* y, const double* z, int64_t np,
+                      int64_t* box_off, int64_t* perm) {
+    int64_t nb[3];
+    for (int a = 0; a < 3; a++) {
+        if (bsize[a] < 1 || n[a] % bsize[a] != 0) return -1;
+        nb[a] = n[a] / bsize[a];
+    }
+    if (dim == 2 && n[1] != 1) return -1;
+    const int64_t nboxes = nb[0] * nb[1] * nb[2];
+    int64_t* box = (int64_t*)malloc((size_t)(np > 0 ? np : 1) * sizeof(int64_t));
+    for (int64_t b = 0; b <= nboxes; b++) box_off[b] = 0;
+    for (int64_t p = 0; p < np; p++) {
+        double pos[3] = {x[p], dim == 3 ? y[p] : 0.0, z[p]};
+        int64_t c[3];
+        for (int a = 0; a < 3; a++) {
+            double dd = (dim == 2 && a == 1) ? 1.0 : d[a];
+            c[a] = wrap((int64_t)floor(pos[a] / dd), n[a]) / bsize[a];
+        }
+        box[p] = (c[2] * nb[1] + c[1]) * nb[0] + c[0];
+        box_off[box[p] + 1]++;
+    }
+    for (int64_t b = 0; b < nboxes; b++) box_off[b + 1] += box_off[b];
+    /* stable placement: particles visited in ascending index */
+    int64_t* fill = (int64_t*)calloc((size_t)nboxes, sizeof(int64_t));
+    for (int64_t p = 0; p < np; p++) perm[box_off[box[p]] + fill[box[p]]++] = p;
+    free(fill);
+    free(box);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Load balancing, Sec. 2.2.                                           */
 /* ------------------------------------------------------------------ */

@@ -70,6 +70,15 @@ int orc_deposit_rho(const orc_sim* s, double* rho_out);
 /* particle count per box; boxes of bsize cells, box index (bz*nby+by)*nbx+bx. */
 int orc_box_counts(const orc_sim* s, const int64_t bsize[3], int64_t* counts_out);
 
+/* box binning of a particle set (Sec. 2.1: a box owns the particles inside
+ * it): box of a particle = floor(x/d) wrapped into [0, n), divided by the box
+ * extent; box index (bz*nby + by)*nbx + bx.  box_off_out: nboxes+1 exclusive
+ * prefix of the per-box counts; perm_out: particle indices in box order, in
+ * ascending original index inside a box (stable). */
+int orc_bin_particles(int dim, const int64_t n[3], const double d[3], const int64_t bsize[3],
+                      const double* x, const double* y, const double* z, int64_t np,
+                      int64_t* box_off_out, int64_t* perm_out);
+
 /* ---- pieces exposed for the pin tests ---- */
 double orc_shape(int order, double dist);     /* B-spline S(dist) */
 /* single-particle gather of all six E/B components at (x,y,z) */

@@ -78,6 +78,7 @@ SIGNATURES = [
     ("pic_read_fields", _int, [_vp, _int, _vp, _int]),
     ("pic_num_particles", _int, [_vp, _int, _pi64]),
     ("pic_read_particles", _int, [_vp, _int, ctypes.POINTER(_vp), _vp, _int]),
+    ("pic_bin_particles", _int, [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _i64, _vp, _vp]),
     ("pic_set_launch", _int, [_vp, ctypes.POINTER(LaunchCfg)]),
     ("pic_get_launch", _int, [_vp, ctypes.POINTER(LaunchCfg)]),
     ("pic_autotune", _int, [_vp, _int, ctypes.POINTER(LaunchCfg)]),

@@ -22,6 +22,7 @@
 
 #include "../../include/pic_api.h"
 #include "pic_balance.h"
+#include "pic_bin.h"
 #include "pic_internal.h"
 
 namespace {
@@ -76,7 +77,7 @@ struct pic_sim {
     int nsm = 0;
     int threads = 256;
     int ctas_per_sm = 1;
-    int split = 4;
+    int split = 16;
     int ctas = 0;
     size_t smem = 0;
     // load balancing
@@ -498,6 +499,11 @@ pic_status replan(pic_sim* s) {
 }
 
 }  // namespace
+
+pic_status pic_record_error(pic_status st, const char* msg) {
+    g_last_error = msg;
+    return st;
+}
 
 // ====================================================================== ABI
 extern "C" {

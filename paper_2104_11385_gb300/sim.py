@@ -218,3 +218,24 @@ def lb_efficiency(costs, assign, n_workers) -> float:
     L.check(lib.pic_lb_efficiency(c.ctypes.data_as(L._pd), a.ctypes.data_as(L._pi32), c.size,
                                   int(n_workers), ctypes.byref(e)))
     return e.value
+
+
+def grid_desc(dim, ncell, box, dx, stream=None) -> L.GridDesc:
+    d = L.GridDesc()
+    d.dim = int(dim)
+    for a in range(3):
+        d.ncell[a] = int(ncell[a])
+        d.box[a] = int(box[a])
+        d.dx[a] = float(dx[a])
+    d.stream = ctypes.c_void_p(stream) if stream else None
+    return d
+
+
+def bin_particles(dim, ncell, box, dx, x, y, z, box_off, perm, stream=None, fn="pic_bin_particles"):
+    """pic_bin_particles on torch CUDA tensors (x, y, z float64; box_off and perm int64)."""
+    lib = L.load()
+    g = grid_desc(dim, ncell, box, dx, stream)
+    yp = ctypes.c_void_p(y.data_ptr()) if y is not None else None
+    L.check(getattr(lib, fn)(ctypes.byref(g), ctypes.c_void_p(x.data_ptr()), yp,
+                             ctypes.c_void_p(z.data_ptr()), int(x.numel()),
+                             ctypes.c_void_p(box_off.data_ptr()), ctypes.c_void_p(perm.data_ptr())))

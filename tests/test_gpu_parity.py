@@ -196,3 +196,44 @@ def test_rho_and_gauss_on_gpu():
     scale = np.abs(sim.read_field(pic.RHO)).max()
     sim.step(6)
     assert np.abs(gauss(sim) - r0).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_bin_particles_against_oracle(dim):
+    import torch
+    from paper_2104_11385_gb300 import sim as S
+    rng = np.random.default_rng(40 + dim)
+    n = (48, 32, 64) if dim == 3 else (64, 1, 96)
+    box = (16, 8, 16) if dim == 3 else (16, 1, 32)
+    dx = (0.3, 0.25, 0.2) if dim == 3 else (0.3, 1.0, 0.2)
+    npart = 200_001
+    L = [n[a] * dx[a] for a in range(3)]
+    x = rng.uniform(-0.2 * L[0], 1.2 * L[0], npart)  # includes periodic images
+    y = rng.uniform(0, L[1], npart) if dim == 3 else np.zeros(npart)
+    z = rng.uniform(0, L[2], npart)
+    off_r, perm_r = orc.bin_particles(dim, n, dx, box, x, y, z)
+    tx, ty, tz = (torch.as_tensor(a, device="cuda") for a in (x, y, z))
+    nb = len(off_r) - 1
+    off = torch.empty(nb + 1, dtype=torch.int64, device="cuda")
+    perm = torch.empty(npart, dtype=torch.int64, device="cuda")
+    S.bin_particles(dim, n, box, dx, tx, ty if dim == 3 else None, tz, off, perm)
+    torch.cuda.synchronize()
+    off_g, perm_g = off.cpu().numpy(), perm.cpu().numpy()
+    assert np.array_equal(off_g, off_r)
+    for b in range(nb):  # same members per box; order inside a box is free
+        sl = slice(off_r[b], off_r[b + 1])
+        assert np.array_equal(np.sort(perm_g[sl]), perm_r[sl])
+
+
+def test_bin_particles_empty_and_errors():
+    import torch
+    from paper_2104_11385_gb300 import sim as S
+    from paper_2104_11385_gb300 import _lib as L
+    z = torch.empty(0, dtype=torch.float64, device="cuda")
+    off = torch.full((4 + 1,), -1, dtype=torch.int64, device="cuda")
+    perm = torch.empty(0, dtype=torch.int64, device="cuda")
+    S.bin_particles(3, (8, 8, 8), (4, 4, 8), (1, 1, 1), z, z, z, off, perm)
+    torch.cuda.synchronize()
+    assert off.cpu().tolist() == [0, 0, 0, 0, 0]
+    with pytest.raises(L.PicError):
+        S.bin_particles(3, (8, 8, 8), (3, 4, 8), (1, 1, 1), z, z, z, off, perm)

@@ -507,3 +507,16 @@ def test_linear_deposit_equals_line_integral_for_in_cell_motion(dim):
                         want[1][kk, jj, ii] = q * w * v[1] / V * _gl3(lambda t: hat(t, 0, ii) * hat(t, 2, kk))
         for c in range(3):
             np.testing.assert_allclose(J[c], want[c], rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------ box binning ---
+def test_bin_particles_by_hand():
+    """4 x 2 x 1 cells in boxes of 2 x 1 x 1 (dx = 0.5): boxes (0,0) (1,0) (0,1) (1,1)."""
+    x = [0.2, 1.9, 0.7, 1.2, 0.4, -0.1, 2.0]   # -0.1 and 2.0 wrap to cells 3 and 0
+    y = [0.1, 0.9, 0.6, 0.2, 0.8, 0.3, 0.7]
+    z = [0.0] * 7
+    off, perm = orc.bin_particles(3, (4, 2, 1), (0.5, 0.5, 0.5), (2, 1, 1), x, y, z)
+    # cells: p0 (0,0) p1 (3,1) p2 (1,1) p3 (2,0) p4 (0,1) p5 (3,0) p6 (0,1)
+    # boxes: p0 0, p1 3, p2 2, p3 1, p4 2, p5 1, p6 2
+    assert list(off) == [0, 1, 3, 6, 7]
+    assert list(perm) == [0, 3, 5, 2, 4, 6, 1]

@@ -15,6 +15,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ETIMEOUT, PIC_ESTATE, PIC_EUNSUPP
 STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ETIMEOUT",
                 -5: "PIC_ESTATE", -6: "PIC_EUNSUPPORTED"}
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
+BIN_NOALLOC_MAX_BOXES = 1 << 20  # PIC_BIN_NOALLOC_MAX_BOXES of include/pic_noalloc.h
 POLICY_KNAPSACK, POLICY_SFC = 0, 1
 COST_HEURISTIC, COST_DEVICE_CLOCK = 0, 1
 LB_NONE, LB_STATIC, LB_DYNAMIC = 0, 1, 2
@@ -79,6 +80,7 @@ SIGNATURES = [
     ("pic_num_particles", _int, [_vp, _int, _pi64]),
     ("pic_read_particles", _int, [_vp, _int, ctypes.POINTER(_vp), _vp, _int]),
     ("pic_bin_particles", _int, [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _i64, _vp, _vp]),
+    ("pic_bin_particles_noalloc", _int, [ctypes.POINTER(GridDesc), _vp, _vp, _vp, _i64, _vp, _vp]),
     ("pic_set_launch", _int, [_vp, ctypes.POINTER(LaunchCfg)]),
     ("pic_get_launch", _int, [_vp, ctypes.POINTER(LaunchCfg)]),
     ("pic_autotune", _int, [_vp, _int, ctypes.POINTER(LaunchCfg)]),

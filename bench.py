@@ -33,9 +33,9 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic FP64 flops per particle update (3D, linear shape): gather 141,
-# Boris push + position 80, Esirkepov weights and currents 213, current adds 54
-FLOPS_PER_PARTICLE = {(3, 1): 488.0, (3, 2): 1090.0, (2, 1): 230.0, (2, 2): 420.0}
+# algorithmic FP64 flops per particle update, in-cell path (3D linear: gather 126,
+# shape weights 12, Boris push 70, Esirkepov deposit 106, positions 3)
+FLOPS_PER_PARTICLE = {(3, 1): 317.0, (3, 2): 793.0, (2, 1): 187.0, (2, 2): 357.0}
 BYTES_PER_PARTICLE = 104.0  # read x,y,z,ux,uy,uz,w (56) + write x..uz (48)
 BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 

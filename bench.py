@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="foil256", choices=["foil256", "uniform32", "lognormal4096"])
     ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (debug only)")
+    ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
+    ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -132,11 +136,13 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, args.scale, seed_offset=rank)
+    args.sched_name = args.sched
     nparts = sum(len(s["x"]) for s in wl["species"])
     ncells = int(math.prod(wl["ncell"]))
     stream = torch.cuda.Stream()
     lbkw = dict(mode=pic.LB_DYNAMIC, interval=10, theta=0.10, policy=pic.POLICY_KNAPSACK,
-                cost=pic.COST_DEVICE_CLOCK, sched=pic.SCHED_LISTS)
+                cost=pic.COST_DEVICE_CLOCK, split=args.split,
+                sched=pic.SCHED_QUEUE if args.sched == "queue" else pic.SCHED_LISTS)
 
     def barrier():
         if world > 1:
@@ -160,6 +166,8 @@ def run_ours(args, rank, world):
 
     # ---- balanced (the paper's dynamic load balancing, on the SMs)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    if args.threads or args.ctas_per_sm:
+        sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
     sim.step(1)                                      # measure per-box clock costs once
     sim.rebalance(**dict(lbkw, theta=0.0))           # initial cost-driven mapping
     sim.set_lb_params(**lbkw)
@@ -174,6 +182,19 @@ def run_ours(args, rank, world):
     sim.set_profiling(False)
     lb = sim.rebalance(**lbkw)
     kernels_per_step = st["launches"] / max(st["steps"], 1)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- the other schedule kind, for the side-by-side line
+    other = "lists" if args.sched == "queue" else "queue"
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    okw = dict(lbkw, sched=pic.SCHED_LISTS if other == "lists" else pic.SCHED_QUEUE)
+    sim.step(1)
+    sim.rebalance(**dict(okw, theta=0.0))
+    sim.set_lb_params(**okw)
+    sim.step(args.warmup)
+    ms_other = timed(sim, args.steps)
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -248,14 +269,17 @@ def run_ours(args, rank, world):
                      "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                              "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE}},
         "static_order": {"value": static_value, "ms_per_step": ms_static / args.steps,
-                         "speedup_balanced_over_static": ms_static / ms_bal},
+                         "speedup_balanced_over_static": ms_static / ms_bal,
+                         "what": "mode NONE: one unit per box, fixed equal-count Morton mapping, per-worker lists"},
+        "other_schedule": {"sched": other, "value": nparts * args.steps * world / (ms_other / 1e3),
+                           "ms_per_step": ms_other / args.steps},
         "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
         "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
                               "sort": st["ms_sort"] / max(st["steps"], 1)},
         "fdtd_cell_updates_per_s": ncells / (st["ms_fields"] / max(st["steps"], 1) / 1e3),
         "lb": {"e_old": lb["e_old"], "e_new": lb["e_new"], "n_units": lb["n_units"],
                "predicted_speedup_sec4": lb["predicted_speedup"]},
-        "config": workload_desc(wl),
+        "config": dict(workload_desc(wl), sched=args.sched),
     }
 
 
@@ -337,7 +361,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded PCG64 workload recipe)",
                 "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
-                "static_order": res["static_order"], "cell_updates_per_s": res["cell_updates_per_s"],
+                "static_order": res["static_order"], "other_schedule": res["other_schedule"],
+                "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
                 "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"]}
         print(json.dumps(line), flush=True)

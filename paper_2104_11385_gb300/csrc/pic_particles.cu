@@ -289,8 +289,11 @@ __device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
 }
 
 // Shared-memory layout: six E/B tiles (TMA destinations), three J tiles, and
-// the queue of cell-crossing particles (struct of arrays, QCAP slots).
-constexpr int QCAP = 512;
+// per-warp ring buffers of cell-crossing particles (struct of arrays, WQ
+// slots per warp, up to 8 warps).
+constexpr int WQ = 64;
+constexpr int QMAXWARPS = 8;
+constexpr int QCAP = WQ * QMAXWARPS;
 constexpr int QF = 8;  // queue fields: xl yl zl dX dY dZ qw vy
 
 struct SmemPlan {
@@ -449,11 +452,11 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 
 // Gather, Boris push, and deposit of one particle.  Particles that keep their
 // support in every direction deposit at once on the small window; the others
-// go to the shared queue, drained in full warps by drain_queue.
+// go to the warp's ring buffer, drained 32 at a time by drain_warp.
 template <int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
                                          const double* __restrict__ sEB, double* __restrict__ sJ,
-                                         double* __restrict__ sQ, int* s_qn, const SmemPlan& P,
+                                         double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                          int64_t p, int32_t* err) {
     double X = sp.cur[0][p], Z = sp.cur[2][p];
     double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
@@ -542,19 +545,17 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     if (same) {
         deposit<DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
     } else {
-        int slot = atomicAdd(s_qn, 1);
-        if (slot < QCAP) {
-            sQ[0 * QCAP + slot] = xl;
-            sQ[1 * QCAP + slot] = yl;
-            sQ[2 * QCAP + slot] = zl;
-            sQ[3 * QCAP + slot] = dX;
-            sQ[4 * QCAP + slot] = dY;
-            sQ[5 * QCAP + slot] = dZ;
-            sQ[6 * QCAP + slot] = qw;
-            sQ[7 * QCAP + slot] = v1;
-        } else {
-            atomicOr(err, PIC_DERR_BOUNDS);  // cannot happen: the queue drains before it fills
-        }
+        // the ring never holds more than 31 + 32 entries: the warp drains 32
+        // whenever 32 are waiting
+        const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
+        sQw[0 * WQ + slot] = xl;
+        sQw[1 * WQ + slot] = yl;
+        sQw[2 * WQ + slot] = zl;
+        sQw[3 * WQ + slot] = dX;
+        sQw[4 * WQ + slot] = dY;
+        sQw[5 * WQ + slot] = dZ;
+        sQw[6 * WQ + slot] = qw;
+        sQw[7 * WQ + slot] = v1;
     }
 
     // ---- new position, boundary, re-sort key
@@ -593,32 +594,33 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     warp_hist_add(sp.count, key);
 }
 
-// Deposits every queued (cell-crossing) particle on the ORDER + 2 window;
-// all threads of the CTA call it together.
+// A warp deposits n <= 32 queued (cell-crossing) particles of its ring,
+// starting at slot head, on the ORDER + 2 window: lane i takes entry head + i.
 template <int DIM, int ORDER>
-__device__ void drain_queue(const SimDev& S, double* __restrict__ sJ, const double* __restrict__ sQ,
-                            int qn, const SmemPlan& P, int32_t* err) {
-    qn = min(qn, QCAP);
-    for (int i = threadIdx.x; i < qn; i += blockDim.x) {
-        const double xl = sQ[0 * QCAP + i], yl = sQ[1 * QCAP + i], zl = sQ[2 * QCAP + i];
-        const double dX = sQ[3 * QCAP + i], dY = sQ[4 * QCAP + i], dZ = sQ[5 * QCAP + i];
-        const double qw = sQ[6 * QCAP + i], vy = sQ[7 * QCAP + i];
-        Support<ORDER> nd[3], mv[3];
-        nd[0] = support<ORDER>(xl);
-        nd[2] = support<ORDER>(zl);
-        mv[0] = support<ORDER>(xl + dX);
-        mv[2] = support<ORDER>(zl + dZ);
-        if (DIM == 3) {
-            nd[1] = support<ORDER>(yl);
-            mv[1] = support<ORDER>(yl + dY);
-        } else {
-            nd[1].s = -1;
-            nd[1].w[0] = 1.0;
-            mv[1] = nd[1];
-        }
-        if (!deposit<DIM, ORDER, ORDER + 2>(S, sJ, P, qw, vy, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]))
-            atomicOr(err, PIC_DERR_BOUNDS);
+__device__ __forceinline__ void drain_warp(const SimDev& S, double* __restrict__ sJ,
+                                           const double* __restrict__ sQw, unsigned head, unsigned n,
+                                           const SmemPlan& P, int32_t* err) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane >= n) return;
+    const unsigned i = (head + lane) & (WQ - 1);
+    const double xl = sQw[0 * WQ + i], yl = sQw[1 * WQ + i], zl = sQw[2 * WQ + i];
+    const double dX = sQw[3 * WQ + i], dY = sQw[4 * WQ + i], dZ = sQw[5 * WQ + i];
+    const double qw = sQw[6 * WQ + i], vy = sQw[7 * WQ + i];
+    Support<ORDER> nd[3], mv[3];
+    nd[0] = support<ORDER>(xl);
+    nd[2] = support<ORDER>(zl);
+    mv[0] = support<ORDER>(xl + dX);
+    mv[2] = support<ORDER>(zl + dZ);
+    if (DIM == 3) {
+        nd[1] = support<ORDER>(yl);
+        mv[1] = support<ORDER>(yl + dY);
+    } else {
+        nd[1].s = -1;
+        nd[1].w[0] = 1.0;
+        mv[1] = nd[1];
     }
+    if (!deposit<DIM, ORDER, ORDER + 2>(S, sJ, P, qw, vy, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]))
+        atomicOr(err, PIC_DERR_BOUNDS);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -637,7 +639,8 @@ __global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __
     // TMA destinations must be 128-byte aligned: round the dynamic base up
     double* smem = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-    __shared__ int s_unit, s_list, s_abort, s_qn;
+    __shared__ int s_unit, s_list, s_abort;
+    __shared__ unsigned s_qhead[QMAXWARPS], s_qtail[QMAXWARPS];
     __shared__ unsigned long long s_cost;
 
     const int nlists = sd->meta[0];
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __
         mbar_init(&bar);
         s_list = my_list;
         s_abort = 0;
-        s_qn = 0;
+        for (int w = 0; w < QMAXWARPS; ++w) s_qhead[w] = s_qtail[w] = 0u;
         s_cost = 0ull;
     }
     __syncthreads();
@@ -729,20 +732,32 @@ __global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __
                     }
                 }
                 const unsigned long long c0 = clock64();
-                double* sQ = sJ + 3 * P.j_stride;
-                for (int64_t base = s0; base < s1; base += blockDim.x) {
-                    const int64_t p = base + threadIdx.x;
-                    if (p < s1) push_one<DIM, ORDER>(S, sp, cur, sEB, sJ, sQ, &s_qn, P, p, sd->err);
-                    __syncthreads();
-                    const int qn = s_qn;
-                    __syncthreads();
-                    // drain the crossing queue when it could overflow next round,
-                    // and always before the segment (and its tile) ends
-                    if (qn > 0 && (qn > QCAP - (int)blockDim.x || base + blockDim.x >= s1)) {
-                        drain_queue<DIM, ORDER>(S, sJ, sQ, qn, P, sd->err);
-                        if (threadIdx.x == 0) s_qn = 0;
-                        __syncthreads();
+                {
+                    // per-warp loop: no CTA barrier until the tile changes
+                    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                    double* sQw = sJ + 3 * P.j_stride + warp * (QF * WQ);
+                    volatile unsigned* vtail = s_qtail + warp;
+                    for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
+                        const int64_t p = p0 + lane;
+                        if (p < s1)
+                            push_one<DIM, ORDER>(S, sp, cur, sEB, sJ, sQw, s_qtail + warp, P, p, sd->err);
+                        __syncwarp();
+                        const unsigned head = s_qhead[warp], tail = *vtail;
+                        if (tail - head >= 32u) {
+                            drain_warp<DIM, ORDER>(S, sJ, sQw, head, 32u, P, sd->err);
+                            __syncwarp();
+                            if (lane == 0) s_qhead[warp] = head + 32u;
+                            __syncwarp();
+                        }
                     }
+                    __syncwarp();
+                    const unsigned head = s_qhead[warp], tail = *vtail;
+                    if (tail != head) {
+                        drain_warp<DIM, ORDER>(S, sJ, sQw, head, tail - head, P, sd->err);
+                        __syncwarp();
+                        if (lane == 0) s_qhead[warp] = tail;
+                    }
+                    __syncwarp();
                 }
                 my_clk += clock64() - c0;
             }

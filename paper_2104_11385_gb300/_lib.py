@@ -62,7 +62,32 @@ class Stats(ctypes.Structure):
                 ("particles_pushed", _i64)]
 
 
-# (name, restype, argtypes) of every exported function of include/pic_api.h
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("dim", _int), ("shape_order", _int), ("max_active", _int), ("hbm_budget_bytes", _i64),
+                ("stream", _vp)]
+
+
+class PlasmaInit(ctypes.Structure):
+    _fields_ = [("ppc", _int), ("density", _d), ("u_th", _d), ("ripple", _d), ("seed", ctypes.c_uint64)]
+
+
+class SpeciesInit(ctypes.Structure):
+    _fields_ = [("charge", _d), ("mass", _d), ("np", _i64), ("soa", _vp * 7), ("ids", _vp)]
+
+
+class RequestDesc(ctypes.Structure):
+    _fields_ = [("grid", GridDesc), ("nsteps", _int), ("plasma", PlasmaInit), ("nspecies", _int),
+                ("species", SpeciesInit * 4)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("ticks", _i64), ("particle_updates", _i64), ("particle_launches", _i64), ("kernels", _i64),
+                ("admitted", _i64), ("finished", _i64), ("bytes_in_use", _i64)]
+
+
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED = range(4)
+
+# (name, restype, argtypes) of every exported function of include/*.h
 SIGNATURES = [
     ("pic_init", _int, [ctypes.POINTER(GridDesc), ctypes.POINTER(_vp)]),
     ("pic_add_species", _int, [_vp, _d, _d, _i64, ctypes.POINTER(_vp), _vp, _int, ctypes.POINTER(_int)]),
@@ -88,6 +113,18 @@ SIGNATURES = [
     ("pic_get_stats", _int, [_vp, ctypes.POINTER(Stats)]),
     ("pic_destroy", _int, [_vp]),
     ("pic_last_error", ctypes.c_char_p, [_vp]),
+    ("pic_server_create", _int, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),
+    ("pic_server_submit", _int, [_vp, ctypes.POINTER(RequestDesc), _pi64]),
+    ("pic_server_tick", _int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    ("pic_server_poll", _int, [_vp, _i64, ctypes.POINTER(_int), _pd, _pd, _pd, ctypes.POINTER(_int)]),
+    ("pic_server_read_fields", _int, [_vp, _i64, _int, _vp]),
+    ("pic_server_num_particles", _int, [_vp, _i64, _int, _pi64]),
+    ("pic_server_read_particles", _int, [_vp, _i64, _int, ctypes.POINTER(_vp), _vp]),
+    ("pic_server_release", _int, [_vp, _i64]),
+    ("pic_server_footprint", _int, [_vp, _i64, _pi64]),
+    ("pic_server_get_stats", _int, [_vp, ctypes.POINTER(ServerStats)]),
+    ("pic_server_destroy", _int, [_vp]),
+    ("pic_server_last_error", ctypes.c_char_p, [_vp]),
 ]
 
 _lib = None

@@ -72,6 +72,7 @@ struct pic_sim {
     int64_t units_cap = 0;
     double rho0 = 0.0;
     std::vector<void*> allocs;
+    int64_t bytes = 0;  // device bytes allocated by the handle
     int64_t np_init[PIC_MAXSP] = {0, 0, 0, 0};
     // launch configuration
     int nsm = 0;
@@ -137,6 +138,7 @@ pic_status dalloc(pic_sim* s, T** p, size_t n) {
         return fail(s, PIC_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     s->allocs.push_back(q);
+    s->bytes += (int64_t)bytes;
     *p = (T*)q;
     return PIC_OK;
 }
@@ -504,6 +506,49 @@ pic_status pic_record_error(pic_status st, const char* msg) {
     g_last_error = msg;
     return st;
 }
+
+// ---- hooks for the request server (same library, not exported) ----
+int64_t pic_internal_bytes(const pic_sim* s) { return s ? s->bytes : 0; }
+
+pic_status pic_internal_mirror(pic_sim* s, SimDev* out) {
+    TRY(check(s));
+    TRY(pull_sim(s));
+    *out = s->h;
+    return PIC_OK;
+}
+
+SimDev* pic_internal_device_sim(pic_sim* s) { return s ? s->d : nullptr; }
+
+// the handle's device state was advanced outside pic_step (request server):
+// never upload the host mirror over it again
+void pic_internal_mark_external(pic_sim* s) {
+    if (s) s->stepped = true;
+}
+
+// device bytes that pic_init + pic_add_species request for this geometry and
+// these species sizes (mirrors the allocations made there)
+int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, int nsp) {
+    int64_t pvol = 1, nboxes = 1, ntiles = 1;
+    for (int a = 0; a < 3; ++a) {
+        const bool act = !(g->dim == 2 && a == 1);
+        const int gw = act ? (a == 0 ? PIC_GX : PIC_G) : 0;
+        pvol *= g->ncell[a] + 2 * gw;
+        const int64_t nb = g->ncell[a] / std::max<int32_t>(1, g->box[a]);
+        nboxes *= nb;
+        const int T = act ? largest_even_divisor_le(g->box[a], g->dim == 3 ? 8 : 16) : 1;
+        ntiles *= nb * (T > 0 ? g->box[a] / T : 1);
+    }
+    auto r = [](int64_t n, int64_t sz) { return std::max<int64_t>(n, 1) * sz; };
+    int64_t b = r(pvol * PIC_NCOMP, 8) + r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) +
+                (int64_t)sizeof(SchedDev) + r(8193, 4) + r(8192, 4) + r(2, 4) + r(4, 8) + r(nboxes, 8);
+    for (int i = 0; i < nsp; ++i) {
+        const int64_t cap = std::max<int64_t>(np[i], 1);
+        b += 14 * r(cap, 8) + 2 * r(cap, 8) + r(cap, 4) + 2 * r(ntiles + 1, 4) + r(ntiles + 2, 8) + 8;
+    }
+    return b;
+}
+
+const char* pic_internal_error(const pic_sim* s) { return s ? s->err.c_str() : g_last_error.c_str(); }
 
 // ====================================================================== ABI
 extern "C" {

@@ -13,9 +13,14 @@ namespace {
 __device__ __forceinline__ int nxt(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 __device__ __forceinline__ int prv(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 
+// multi-simulation launches: blockIdx.y indexes the slot list (nullptr: slot 0)
+__device__ __forceinline__ const SimDev& slot_sim(const SimDev* sims, const int* slots) {
+    return sims[slots ? slots[blockIdx.y] : 0];
+}
+
 template <int DIM>
-__global__ void b_half_kernel(const SimDev* __restrict__ sims) {
-    const SimDev& S = sims[0];
+__global__ void b_half_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
+    const SimDev& S = slot_sim(sims, slots);
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const int64_t ncell = (int64_t)nx * ny * nz;
     const double h = 0.5 * S.dt;
@@ -46,8 +51,8 @@ __global__ void b_half_kernel(const SimDev* __restrict__ sims) {
 }
 
 template <int DIM>
-__global__ void e_kernel(const SimDev* __restrict__ sims) {
-    const SimDev& S = sims[0];
+__global__ void e_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
+    const SimDev& S = slot_sim(sims, slots);
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const int64_t ncell = (int64_t)nx * ny * nz;
     const double dt = S.dt;
@@ -95,9 +100,10 @@ __global__ void e_kernel(const SimDev* __restrict__ sims) {
 }
 
 // E and B of cell layer k scaled by 1 - 0.5 (p/A)^2, p = depth inside the layer
-__global__ void damp_kernel(const SimDev* __restrict__ sims) {
-    const SimDev& S = sims[0];
+__global__ void damp_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
+    const SimDev& S = slot_sim(sims, slots);
     const int A = S.absorb;
+    if (A <= 0) return;
     const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
     const int64_t per_layer = (int64_t)nx * ny;
     const int64_t total = per_layer * 2 * A;
@@ -117,8 +123,9 @@ __global__ void damp_kernel(const SimDev* __restrict__ sims) {
 }
 
 // periodic images into the guard cells of components [c0, c0+nc)
-__global__ void guard_kernel(const SimDev* __restrict__ sims, int c0, int nc) {
-    const SimDev& S = sims[0];
+__global__ void guard_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots, int c0,
+                             int nc) {
+    const SimDev& S = slot_sim(sims, slots);
     const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
     const int64_t pvol = (int64_t)px * py * pz;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pvol;
@@ -201,6 +208,16 @@ __global__ void rho_kernel(const SimDev* __restrict__ sims, int sp_idx, double* 
     }
 }
 
+// zeroes the J block (three padded arrays) of every listed simulation
+__global__ void zero_j_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
+    const SimDev& S = slot_sim(sims, slots);
+    const int64_t n = (int64_t)S.pn[0] * S.pn[1] * S.pn[2] * 3;
+    double* J = S.F[6];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        J[i] = 0.0;
+}
+
 __global__ void fill_kernel(double* p, int64_t n, double v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -220,17 +237,17 @@ cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t 
     const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
     const int nb = blocks_for(ncell, 256);
     if (h.dim == 3) {
-        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim);
-        e_kernel<3><<<nb, 256, 0, st>>>(dsim);
-        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim);
+        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
+        e_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
+        b_half_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
     } else {
-        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim);
-        e_kernel<2><<<nb, 256, 0, st>>>(dsim);
-        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim);
+        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim, nullptr);
+        e_kernel<2><<<nb, 256, 0, st>>>(dsim, nullptr);
+        b_half_kernel<2><<<nb, 256, 0, st>>>(dsim, nullptr);
     }
     if (h.absorb > 0) {
         int64_t t = (int64_t)h.n[0] * h.n[1] * 2 * h.absorb;
-        damp_kernel<<<blocks_for(t, 256), 256, 0, st>>>(dsim);
+        damp_kernel<<<blocks_for(t, 256), 256, 0, st>>>(dsim, nullptr);
     }
     return pic_launch_guards(dsim, h, 0, 6, st);
 }
@@ -238,7 +255,35 @@ cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t 
 cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& h, int c0, int nc,
                               cudaStream_t st) {
     const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
-    guard_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, c0, nc);
+    guard_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr, c0, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_fields_multi(const SimDev* sims, const int* slots, int nslots, int dim,
+                                    int64_t max_cells, int64_t max_padded, bool any_absorb,
+                                    cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    const dim3 g(blocks_for(max_cells, 256) / 4 + 1, nslots);
+    if (dim == 3) {
+        b_half_kernel<3><<<g, 256, 0, st>>>(sims, slots);
+        e_kernel<3><<<g, 256, 0, st>>>(sims, slots);
+        b_half_kernel<3><<<g, 256, 0, st>>>(sims, slots);
+    } else {
+        b_half_kernel<2><<<g, 256, 0, st>>>(sims, slots);
+        e_kernel<2><<<g, 256, 0, st>>>(sims, slots);
+        b_half_kernel<2><<<g, 256, 0, st>>>(sims, slots);
+    }
+    if (any_absorb) damp_kernel<<<g, 256, 0, st>>>(sims, slots);
+    const dim3 gp(blocks_for(max_padded, 256) / 4 + 1, nslots);
+    guard_kernel<<<gp, 256, 0, st>>>(sims, slots, 0, 6);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_zero_j_multi(const SimDev* sims, const int* slots, int nslots,
+                                    int64_t max_padded, cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    const dim3 g(blocks_for(3 * max_padded, 256) / 4 + 1, nslots);
+    zero_j_kernel<<<g, 256, 0, st>>>(sims, slots);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pic_api.h"
+
 #define PIC_G 2        // guard cells per side in y and z of the padded field arrays
 #define PIC_GX 3       // guard cells per side in x: odd, so that a tile's TMA box, which
                        // starts one cell below an even tile origin, starts at an even
@@ -122,6 +124,26 @@ cudaError_t pic_launch_pad(const double* dense, double* padded, const SimDev& hs
                            cudaStream_t st);
 cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& hsim, int first_comp,
                               int ncomp, cudaStream_t st);
+// multi-simulation launches over a device list of slots (blockIdx.y = slot)
+cudaError_t pic_launch_fields_multi(const SimDev* sims, const int* slots, int nslots, int dim,
+                                    int64_t max_cells, int64_t max_padded, bool any_absorb,
+                                    cudaStream_t st);
+cudaError_t pic_launch_zero_j_multi(const SimDev* sims, const int* slots, int nslots,
+                                    int64_t max_padded, cudaStream_t st);
+cudaError_t pic_launch_sort_multi(SimDev* sims, const int* slots, int nslots, int dim, int64_t max_cap,
+                                  cudaStream_t st);
+cudaError_t pic_launch_finish_multi(SimDev* sims, const int* slots, int nslots, const SchedDev* sched,
+                                    cudaStream_t st);
 cudaError_t pic_launch_to_cells(double* p, int64_t np, double d, int n, cudaStream_t st);
 cudaError_t pic_launch_from_cells(const double* src, double* dst, int64_t np, double d,
                                   cudaStream_t st);
+
+// hooks of pic_api.cu used by the request server (not part of the C ABI)
+int64_t pic_internal_bytes(const pic_sim* s);
+pic_status pic_internal_mirror(pic_sim* s, SimDev* out);
+SimDev* pic_internal_device_sim(pic_sim* s);
+void pic_internal_mark_external(pic_sim* s);
+// records the message returned by pic_last_error(NULL) on this thread
+pic_status pic_record_error(pic_status st, const char* msg);
+int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, int nsp);
+const char* pic_internal_error(const pic_sim* s);

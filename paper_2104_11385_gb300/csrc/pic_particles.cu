@@ -782,8 +782,13 @@ __global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __
 // ---------------------------------------------------------------------------
 // re-sort: scan of the per-tile histogram, scatter, end-of-step bookkeeping
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) pic_scan_kernel(SimDev* __restrict__ sims, int sp_idx) {
-    SimDev& S = sims[0];
+// multi-simulation launches: blockIdx.y indexes the slot list (nullptr: slot 0);
+// sp_idx < 0 takes the species from blockIdx.x (scan, swap) or blockIdx.z (scatter)
+__global__ void __launch_bounds__(1024) pic_scan_kernel(SimDev* __restrict__ sims,
+                                                        const int* __restrict__ slots, int sp_idx) {
+    SimDev& S = sims[slots ? slots[blockIdx.y] : 0];
+    if (sp_idx < 0) sp_idx = blockIdx.x;
+    if (sp_idx >= S.nsp) return;
     SpeciesDev& sp = S.sp[sp_idx];
     const int N = S.ntiles + 1;  // tiles plus the bucket of removed particles
     __shared__ int64_t s_part[1024];
@@ -815,8 +820,10 @@ __global__ void __launch_bounds__(1024) pic_scan_kernel(SimDev* __restrict__ sim
 }
 
 template <int DIM>
-__global__ void pic_scatter_kernel(SimDev* __restrict__ sims, int sp_idx) {
-    const SimDev& S = sims[0];
+__global__ void pic_scatter_kernel(SimDev* __restrict__ sims, const int* __restrict__ slots, int sp_idx) {
+    const SimDev& S = sims[slots ? slots[blockIdx.y] : 0];
+    if (sp_idx < 0) sp_idx = blockIdx.z;
+    if (sp_idx >= S.nsp) return;
     const SpeciesDev& sp = S.sp[sp_idx];
     const int64_t np = *sp.np_prev;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -847,8 +854,11 @@ __global__ void pic_scatter_kernel(SimDev* __restrict__ sims, int sp_idx) {
     }
 }
 
-__global__ void pic_swap_kernel(SimDev* __restrict__ sims, int sp_idx) {
-    SpeciesDev& sp = sims[0].sp[sp_idx];
+__global__ void pic_swap_kernel(SimDev* __restrict__ sims, const int* __restrict__ slots, int sp_idx) {
+    SimDev& S = sims[slots ? slots[blockIdx.y] : 0];
+    if (sp_idx < 0) sp_idx = blockIdx.x;
+    if (sp_idx >= S.nsp || threadIdx.x != 0) return;
+    SpeciesDev& sp = S.sp[sp_idx];
     for (int a = 0; a < 7; ++a) {
         double* t = sp.cur[a];
         sp.cur[a] = sp.alt[a];
@@ -859,10 +869,13 @@ __global__ void pic_swap_kernel(SimDev* __restrict__ sims, int sp_idx) {
     sp.id_alt = ti;
 }
 
-__global__ void pic_finish_kernel(SimDev* __restrict__ sims, const SchedDev* __restrict__ sd) {
-    const int nlists = sd->meta[0];
-    for (int i = threadIdx.x; i < nlists; i += blockDim.x) sd->head[i] = 0;
-    if (threadIdx.x == 0) *sims[0].step += 1;
+__global__ void pic_finish_kernel(SimDev* __restrict__ sims, const int* __restrict__ slots,
+                                  const SchedDev* __restrict__ sd) {
+    if (blockIdx.y == 0) {
+        const int nlists = sd->meta[0];
+        for (int i = threadIdx.x; i < nlists; i += blockDim.x) sd->head[i] = 0;
+    }
+    if (threadIdx.x == 0) *sims[slots ? slots[blockIdx.y] : 0].step += 1;
 }
 
 template <int DIM>
@@ -976,11 +989,29 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t pic_launch_sort(const SimDev* dsim, const SimDev& hsim, int sp, cudaStream_t st) {
     SimDev* d = const_cast<SimDev*>(dsim);
-    pic_scan_kernel<<<1, 1024, 0, st>>>(d, sp);
+    pic_scan_kernel<<<1, 1024, 0, st>>>(d, nullptr, sp);
     int64_t cap = hsim.sp[sp].cap;
-    if (hsim.dim == 3) pic_scatter_kernel<3><<<grid_for(cap, 256), 256, 0, st>>>(d, sp);
-    else pic_scatter_kernel<2><<<grid_for(cap, 256), 256, 0, st>>>(d, sp);
-    pic_swap_kernel<<<1, 1, 0, st>>>(d, sp);
+    if (hsim.dim == 3) pic_scatter_kernel<3><<<grid_for(cap, 256), 256, 0, st>>>(d, nullptr, sp);
+    else pic_scatter_kernel<2><<<grid_for(cap, 256), 256, 0, st>>>(d, nullptr, sp);
+    pic_swap_kernel<<<1, 32, 0, st>>>(d, nullptr, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_sort_multi(SimDev* sims, const int* slots, int nslots, int dim, int64_t max_cap,
+                                  cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    pic_scan_kernel<<<dim3(PIC_MAXSP, nslots), 1024, 0, st>>>(sims, slots, -1);
+    const dim3 g(grid_for(max_cap, 256) / 4 + 1, nslots, PIC_MAXSP);
+    if (dim == 3) pic_scatter_kernel<3><<<g, 256, 0, st>>>(sims, slots, -1);
+    else pic_scatter_kernel<2><<<g, 256, 0, st>>>(sims, slots, -1);
+    pic_swap_kernel<<<dim3(PIC_MAXSP, nslots), 32, 0, st>>>(sims, slots, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_finish_multi(SimDev* sims, const int* slots, int nslots, const SchedDev* sched,
+                                    cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    pic_finish_kernel<<<dim3(1, nslots), 256, 0, st>>>(sims, slots, sched);
     return cudaGetLastError();
 }
 
@@ -995,7 +1026,7 @@ cudaError_t pic_launch_initial_keys(const SimDev* dsim, const SimDev& hsim, int 
 }
 
 cudaError_t pic_launch_finish(SimDev* dsim, const SchedDev* sched, cudaStream_t st) {
-    pic_finish_kernel<<<1, 256, 0, st>>>(dsim, sched);
+    pic_finish_kernel<<<1, 256, 0, st>>>(dsim, nullptr, sched);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in declared if not hasattr(lib, n)]
     assert not missing, missing
     bound = {n for n, _, _ in L.SIGNATURES}
-    assert declared <= bound | {"pic_last_error"}
+    assert declared <= bound | {"pic_last_error"}, declared - bound
 
 
 def test_struct_layouts_match_header_sizes():

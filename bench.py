@@ -34,8 +34,8 @@ HBM_FALLBACK_GBS = 6800.0
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic FP64 flops per particle update, in-cell path (3D linear: gather 126,
-# shape weights 12, Boris push 70, Esirkepov deposit 106, positions 3)
-FLOPS_PER_PARTICLE = {(3, 1): 317.0, (3, 2): 793.0, (2, 1): 187.0, (2, 2): 357.0}
+# local positions and half-node shifts 6, Boris push 70, Esirkepov deposit 73, positions 3)
+FLOPS_PER_PARTICLE = {(3, 1): 278.0, (3, 2): 766.0, (2, 1): 170.0, (2, 2): 350.0}
 BYTES_PER_PARTICLE = 104.0  # read x,y,z,ux,uy,uz,w (56) + write x..uz (48)
 BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-server", action="store_true")
+    ap.add_argument("--server-requests", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -283,6 +285,63 @@ def run_ours(args, rank, world):
     }
 
 
+def run_server(args, seed=4):
+    """Serving arm: independent 2D3V thermal-plasma requests (grid side in
+    {64,128,256,512}, ppc in {1,..,64}, steps U[100, 400]: the serving workload
+    with shortened runs) through the continuous-batching server; first all at
+    once (saturated throughput), then Poisson arrivals at 0.8x that rate."""
+    import numpy as np
+    from paper_2104_11385_gb300.server import Server
+    from paper_2104_11385_gb300 import _lib as L
+    rng = np.random.default_rng(seed)
+    n = args.server_requests
+    reqs = []
+    for i in range(n):
+        side = int(rng.choice([64, 128, 256, 512]))
+        ppc = int(rng.choice([1, 2, 4, 8, 16, 32, 64]))
+        steps = int(rng.integers(100, 401))
+        reqs.append(dict(ncell=(side, 1, side), box=(32, 1, 32), dx=(0.2, 1.0, 0.2), nsteps=steps,
+                         plasma=dict(ppc=ppc, density=1.0, u_th=0.02, ripple=0.01, seed=1000 + i)))
+    work = sum(r["ncell"][0] * r["ncell"][2] * r["plasma"]["ppc"] * r["nsteps"] for r in reqs)
+
+    def serve(arrivals):
+        srv = Server(dim=2, max_active=64, hbm_budget_bytes=160 << 30)
+        t0 = time.perf_counter()
+        ids, k, done = {}, 0, {}
+        while len(done) < n:
+            now = time.perf_counter() - t0
+            while k < n and arrivals[k] <= now:
+                ids[srv.submit(**reqs[k])] = k
+                k += 1
+            a, p = srv.tick()
+            for rid, i in list(ids.items()):
+                st = srv.poll(rid)
+                if st["state"] == L.REQ_DONE:
+                    done[i] = st["t_done"] - st["t_submit"]
+                    srv.release(rid)
+                    del ids[rid]
+            if a == 0 and p == 0 and k < n:
+                time.sleep(max(0.0, min(0.05, arrivals[k] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([done[i] for i in range(n)])
+        return wall, lat, stats
+
+    wall_sat, lat_sat, st_sat = serve([0.0] * n)
+    sat_rate = n / wall_sat
+    lam = 0.8 * sat_rate
+    arr = np.cumsum(rng.exponential(1.0 / lam, n))
+    arr -= arr[0]
+    wall, lat, st = serve(list(arr))
+    return {"requests": n, "mix": "2D3V, side {64..512}, ppc {1..64}, steps U[100,400], 32x32 boxes",
+            "saturated_requests_per_s": sat_rate, "saturated_particle_updates_per_s": work / wall_sat,
+            "poisson_lambda_per_s": lam, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "throughput_requests_per_s": n / wall, "throughput_particle_updates_per_s": work / wall,
+            "ticks": st["ticks"], "packed_particle_launches": st["particle_launches"]}
+
+
 def oracle_rate(wl_name, budget_s=15.0, steps=1):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload:
     the same recipe at 1/4 of the extents (1/64 of the cells, the foil 2 cells
@@ -349,6 +408,9 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     res = run_ours(args, rank, world)
+    server = None
+    if rank == 0 and not args.no_server:
+        server = run_server(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=6)
@@ -364,7 +426,7 @@ def main():
                 "static_order": res["static_order"], "other_schedule": res["other_schedule"],
                 "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
-                "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"]}
+                "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"], "server": server}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -80,6 +80,7 @@ struct pic_sim {
     int ctas_per_sm = 1;
     int split = 16;
     int ctas = 0;
+    int minb = 1;
     size_t smem = 0;
     // load balancing
     pic_lb_params lb{};
@@ -420,7 +421,7 @@ pic_status enqueue_step(pic_sim* s, bool with_events) {
     if (with_events) CU(s, cudaEventRecord(s->ev[0], s->stream));
     CU(s, cudaMemsetAsync(h.F[6], 0, jbytes, s->stream));
     if (h.nsp > 0) {
-        LaunchCfg cfg{s->threads, s->ctas};
+        LaunchCfg cfg{s->threads, s->ctas, s->minb};
         CU(s, pic_launch_particles(h.dim, h.order, cfg, s->smem, s->ds, s->d, s->stream));
     }
     if (with_events) CU(s, cudaEventRecord(s->ev[1], s->stream));
@@ -457,14 +458,16 @@ pic_status capture_graph(pic_sim* s) {
 }
 
 pic_status configure_launch(pic_sim* s) {
-    s->smem = pic_particle_smem_bytes(s->h.dim, s->h.order, s->h.T);
+    s->smem = pic_particle_smem_bytes(s->h.dim, s->h.order, s->h.T, s->threads);
     cudaDeviceProp prop;
     CU(s, cudaGetDeviceProperties(&prop, s->device));
     if (s->smem > prop.sharedMemPerBlockOptin)
         return fail(s, PIC_EUNSUPPORTED, "tile needs %zu bytes of shared memory", s->smem);
     CU(s, pic_prepare_particles(s->h.dim, s->h.order, s->smem));
     // persistent grid: every CTA resident (registers, shared memory, threads)
-    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->threads, s->smem);
+    // ctas_per_sm >= 2 selects the kernel variant compiled for 2 resident CTAs
+    s->minb = s->ctas_per_sm >= 2 ? 2 : 1;
+    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->minb, s->threads, s->smem);
     if (resident < 1) return fail(s, PIC_EUNSUPPORTED, "particle kernel does not fit on an SM");
     int per_sm = std::max(1, std::min(s->ctas_per_sm, resident));
     s->ctas = s->nsm * per_sm;

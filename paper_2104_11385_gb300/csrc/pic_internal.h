@@ -103,10 +103,11 @@ __host__ __device__ inline int64_t pidx(const SimDev& s, int i, int j, int k) {
 struct LaunchCfg {
     int threads;
     int ctas;
+    int minb;  // register budget variant of the particle kernel: 1 or 2 CTAs per SM
 };
-size_t pic_particle_smem_bytes(int dim, int order, const int T[3]);
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads);
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem);  // outside graph capture
-int pic_particle_occupancy(int dim, int order, int threads, size_t smem);  // resident CTAs per SM
+int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem);  // resident CTAs per SM
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
                                  const SchedDev* sched, SimDev* sims, cudaStream_t st);
 cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& hsim, cudaStream_t st);

@@ -18,8 +18,6 @@
 
 namespace {
 
-constexpr double kThird = 1.0 / 3.0;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -193,7 +191,24 @@ __device__ __forceinline__ double interp(const double* __restrict__ F, int SX, i
                                          const Support<ORDER>& sx, const Support<ORDER>& sy,
                                          const Support<ORDER>& sz) {
     // tile column 0 is local cell -1
-    if (DIM == 3) {
+    if (ORDER == 1) {
+        // linear: nested lerps a + f (b - a) need only the fractional parts
+        auto lerp = [](double a, double b, double f) { return fma(f, b - a, a); };
+        const double fx = sx.w[1];
+        if (DIM == 3) {
+            const double* r00 = F + ((sz.s + 1) * SY + (sy.s + 1)) * SX + (sx.s + 1);
+            const double* r10 = r00 + SX;
+            const double* r01 = r00 + SX * SY;
+            const double* r11 = r01 + SX;
+            const double a0 = lerp(lerp(r00[0], r00[1], fx), lerp(r10[0], r10[1], fx), sy.w[1]);
+            const double a1 = lerp(lerp(r01[0], r01[1], fx), lerp(r11[0], r11[1], fx), sy.w[1]);
+            return lerp(a0, a1, sz.w[1]);
+        } else {
+            const double* r0 = F + (sz.s + 1) * SX + (sx.s + 1);
+            const double* r1 = r0 + SX;
+            return lerp(lerp(r0[0], r0[1], fx), lerp(r1[0], r1[1], fx), sz.w[1]);
+        }
+    } else if (DIM == 3) {
         double acc = 0.0;
 #pragma unroll
         for (int c = 0; c <= ORDER; ++c) {
@@ -293,8 +308,11 @@ __device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
 // slots per warp, up to 8 warps).
 constexpr int WQ = 64;
 constexpr int QMAXWARPS = 8;
-constexpr int QCAP = WQ * QMAXWARPS;
-constexpr int QF = 8;  // queue fields: xl yl zl dX dY dZ qw vy
+// queue fields: 0 xl, 1 zl, 2 dX, 3 dZ, 4 qw, 5 yl (3D) or vy (2D), 6 dY (3D)
+template <int DIM>
+struct QFields {
+    static constexpr int n = DIM == 3 ? 7 : 6;
+};
 
 struct SmemPlan {
     int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
@@ -309,7 +327,7 @@ __host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3])
     p.j_vol = js[0] * js[1] * js[2];
     p.eb_stride = (p.eb_vol + 15) & ~15;
     p.j_stride = (p.j_vol + 1) & ~1;
-    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride + QF * QCAP) * sizeof(double);
+    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
     return p;
 }
 
@@ -347,20 +365,21 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
     double* Jx = sJ;
     double* Jy = sJ + P.j_stride;
     double* Jz = sJ + 2 * P.j_stride;
-    double Ax[W], Cx[W], Az[W];
+    // transverse weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3
+    //   = A_a A_b + DS_a DS_b / 12   with A = S0 + DS/2
+    constexpr double k12 = 1.0 / 12.0;
+    double Ax[W], Az[W], Dx12[W], Dz12[W];
 #pragma unroll
     for (int l = 0; l < W; ++l) {
         Ax[l] = fma(0.5, wx.DS[l], wx.S0[l]);
-        Cx[l] = fma(kThird, wx.DS[l], 0.5 * wx.S0[l]);
         Az[l] = fma(0.5, wz.DS[l], wz.S0[l]);
+        Dx12[l] = k12 * wx.DS[l];
+        Dz12[l] = k12 * wz.DS[l];
     }
     if (DIM == 3) {
-        double Ay[W], Cy[W];
+        double Ay[W];
 #pragma unroll
-        for (int l = 0; l < W; ++l) {
-            Ay[l] = fma(0.5, wy.DS[l], wy.S0[l]);
-            Cy[l] = fma(kThird, wy.DS[l], 0.5 * wy.S0[l]);
-        }
+        for (int l = 0; l < W; ++l) Ay[l] = fma(0.5, wy.DS[l], wy.S0[l]);
         const int bx = wx.base + lo, by = wy.base + lo, bz = wz.base + lo;
         {
             const double c = qw * S.jfac[0];
@@ -372,7 +391,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             for (int k = 0; k < W; ++k)
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    double T = fma(Ay[j], wz.S0[k], Cy[j] * wz.DS[k]);
+                    double T = fma(Ay[j], Az[k], wy.DS[j] * Dz12[k]);
                     double* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) atomicAdd(row + l, Pf[l] * T);
@@ -388,7 +407,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             for (int k = 0; k < W; ++k)
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
-                    double T = fma(Ax[i], wz.S0[k], Cx[i] * wz.DS[k]);
+                    double T = fma(Ax[i], Az[k], wx.DS[i] * Dz12[k]);
                     double* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
 #pragma unroll
                     for (int j = 0; j < W - 1; ++j) atomicAdd(col + j * jx, Pf[j] * T);
@@ -404,7 +423,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             for (int j = 0; j < W; ++j)
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
-                    double T = fma(Ax[i], wy.S0[j], Cx[i] * wy.DS[j]);
+                    double T = fma(Ax[i], Ay[j], Dx12[i] * wy.DS[j]);
                     double* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
 #pragma unroll
                     for (int k = 0; k < W - 1; ++k) atomicAdd(col + k * jx * jy, Pf[k] * T);
@@ -438,16 +457,91 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
                 for (int k = 0; k < W - 1; ++k) atomicAdd(col + k * jx, Pf[k] * Ax[i]);
             }
         }
-        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax S0z + Cx DSz)
+        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax Az + DSx DSz / 12)
             const double c = qw * vy * S.jyfac2d;
 #pragma unroll
             for (int k = 0; k < W; ++k)
 #pragma unroll
                 for (int i = 0; i < W; ++i)
-                    atomicAdd(Jy + (bz + k) * jx + (bx + i), c * fma(Ax[i], wz.S0[k], Cx[i] * wz.DS[k]));
+                    atomicAdd(Jy + (bz + k) * jx + (bx + i), c * fma(Ax[i], Az[k], Dx12[i] * wz.DS[k]));
         }
     }
     return true;
+}
+
+// Linear shapes, particle keeping its cell in every direction: the window is
+// the two nodes of the cell, DS = (-d, d) with d = f1 - f0, so the prefix sum
+// has one term and the transverse weight A_a A_b + DS_a DS_b / 12 is
+// A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
+// deposit<DIM, 1, 2>, with fewer FP64 instructions.
+template <int DIM>
+__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __restrict__ sJ,
+                                                   const SmemPlan& P, double qw, double vy,
+                                                   const Support<1>* n, const Support<1>* m) {
+    constexpr double k12 = 1.0 / 12.0;
+    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    double* Jx = sJ;
+    double* Jy = sJ + P.j_stride;
+    double* Jz = sJ + 2 * P.j_stride;
+    const double dx = m[0].w[1] - n[0].w[1], dz = m[2].w[1] - n[2].w[1];
+    const double mx = fma(0.5, dx, n[0].w[1]), mz = fma(0.5, dz, n[2].w[1]);
+    const double ax0 = 1.0 - mx, az0 = 1.0 - mz;
+    const int bx = n[0].s + lo, bz = n[2].s + lo;
+    if (DIM == 3) {
+        const double dy = m[1].w[1] - n[1].w[1];
+        const double my = fma(0.5, dy, n[1].w[1]);
+        const double ay0 = 1.0 - my;
+        const int by = n[1].s + lo;
+        {   // Jx at (bx, by + j, bz + k)
+            const double e = (dy * dz) * k12;
+            const double pf = -(qw * S.jfac[0]) * dx;
+            double* r = Jx + (bz * jy + by) * jx + bx;
+            atomicAdd(r, pf * fma(ay0, az0, e));
+            atomicAdd(r + jx, pf * fma(my, az0, -e));
+            atomicAdd(r + jx * jy, pf * fma(ay0, mz, -e));
+            atomicAdd(r + jx * jy + jx, pf * fma(my, mz, e));
+        }
+        {   // Jy at (bx + i, by, bz + k)
+            const double e = (dx * dz) * k12;
+            const double pf = -(qw * S.jfac[1]) * dy;
+            double* r = Jy + (bz * jy + by) * jx + bx;
+            atomicAdd(r, pf * fma(ax0, az0, e));
+            atomicAdd(r + 1, pf * fma(mx, az0, -e));
+            atomicAdd(r + jx * jy, pf * fma(ax0, mz, -e));
+            atomicAdd(r + jx * jy + 1, pf * fma(mx, mz, e));
+        }
+        {   // Jz at (bx + i, by + j, bz)
+            const double e = (dx * dy) * k12;
+            const double pf = -(qw * S.jfac[2]) * dz;
+            double* r = Jz + (bz * jy + by) * jx + bx;
+            atomicAdd(r, pf * fma(ax0, ay0, e));
+            atomicAdd(r + 1, pf * fma(mx, ay0, -e));
+            atomicAdd(r + jx, pf * fma(ax0, my, -e));
+            atomicAdd(r + jx + 1, pf * fma(mx, my, e));
+        }
+    } else {
+        {   // Jx at (bx, bz + k): -(q w/(dz dt)) DSx A_z
+            const double pf = -(qw * S.jfac[0]) * dx;
+            double* r = Jx + bz * jx + bx;
+            atomicAdd(r, pf * az0);
+            atomicAdd(r + jx, pf * mz);
+        }
+        {   // Jz at (bx + i, bz)
+            const double pf = -(qw * S.jfac[2]) * dz;
+            double* r = Jz + bz * jx + bx;
+            atomicAdd(r, pf * ax0);
+            atomicAdd(r + 1, pf * mx);
+        }
+        {   // out-of-plane Jy at (bx + i, bz + k)
+            const double e = (dx * dz) * k12;
+            const double c = qw * vy * S.jyfac2d;
+            double* r = Jy + bz * jx + bx;
+            atomicAdd(r, c * fma(ax0, az0, e));
+            atomicAdd(r + 1, c * fma(mx, az0, -e));
+            atomicAdd(r + jx, c * fma(ax0, mz, -e));
+            atomicAdd(r + jx + 1, c * fma(mx, mz, e));
+        }
+    }
 }
 
 // Gather, Boris push, and deposit of one particle.  Particles that keep their
@@ -543,19 +637,21 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     const double qw = sp.q * w;
     bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
     if (same) {
-        deposit<DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
+        if constexpr (ORDER == 1)
+            deposit_lin_incell<DIM>(S, sJ, P, qw, v1, nd, mv);
+        else
+            deposit<DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
     } else {
         // the ring never holds more than 31 + 32 entries: the warp drains 32
         // whenever 32 are waiting
         const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
         sQw[0 * WQ + slot] = xl;
-        sQw[1 * WQ + slot] = yl;
-        sQw[2 * WQ + slot] = zl;
-        sQw[3 * WQ + slot] = dX;
-        sQw[4 * WQ + slot] = dY;
-        sQw[5 * WQ + slot] = dZ;
-        sQw[6 * WQ + slot] = qw;
-        sQw[7 * WQ + slot] = v1;
+        sQw[1 * WQ + slot] = zl;
+        sQw[2 * WQ + slot] = dX;
+        sQw[3 * WQ + slot] = dZ;
+        sQw[4 * WQ + slot] = qw;
+        sQw[5 * WQ + slot] = DIM == 3 ? yl : v1;
+        if (DIM == 3) sQw[6 * WQ + slot] = dY;
     }
 
     // ---- new position, boundary, re-sort key
@@ -603,9 +699,10 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, double* __restrict__
     const unsigned lane = threadIdx.x & 31u;
     if (lane >= n) return;
     const unsigned i = (head + lane) & (WQ - 1);
-    const double xl = sQw[0 * WQ + i], yl = sQw[1 * WQ + i], zl = sQw[2 * WQ + i];
-    const double dX = sQw[3 * WQ + i], dY = sQw[4 * WQ + i], dZ = sQw[5 * WQ + i];
-    const double qw = sQw[6 * WQ + i], vy = sQw[7 * WQ + i];
+    const double xl = sQw[0 * WQ + i], zl = sQw[1 * WQ + i];
+    const double dX = sQw[2 * WQ + i], dZ = sQw[3 * WQ + i], qw = sQw[4 * WQ + i];
+    const double yl = DIM == 3 ? sQw[5 * WQ + i] : 0.0, vy = DIM == 3 ? 0.0 : sQw[5 * WQ + i];
+    const double dY = DIM == 3 ? sQw[6 * WQ + i] : 0.0;
     Support<ORDER> nd[3], mv[3];
     nd[0] = support<ORDER>(xl);
     nd[2] = support<ORDER>(zl);
@@ -631,9 +728,11 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 }  // namespace
 
-template <int DIM, int ORDER>
-__global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __restrict__ sd,
-                                                           SimDev* __restrict__ sims) {
+// MINB = resident CTAs per SM the register allocation is sized for (1: up to
+// 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM)
+template <int DIM, int ORDER, int MINB>
+__global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
+                                                              SimDev* __restrict__ sims) {
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -735,7 +834,7 @@ __global__ void __launch_bounds__(256, 1) pic_particle_kernel(const SchedDev* __
                 {
                     // per-warp loop: no CTA barrier until the tile changes
                     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                    double* sQw = sJ + 3 * P.j_stride + warp * (QF * WQ);
+                    double* sQw = sJ + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
                     volatile unsigned* vtail = s_qtail + warp;
                     for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
                         const int64_t p = p0 + lane;
@@ -926,7 +1025,7 @@ __global__ void pic_scale_copy_kernel(const double* __restrict__ s, double* __re
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-size_t pic_particle_smem_bytes(int dim, int order, const int T[3]) {
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads) {
     int ebs[3], js[3];
     for (int a = 0; a < 3; ++a) {
         bool act = !(dim == 2 && a == 1);
@@ -934,41 +1033,17 @@ size_t pic_particle_smem_bytes(int dim, int order, const int T[3]) {
         js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
     }
     if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
-    return smem_plan(ebs, js).bytes + 128;  // + alignment slack of the dynamic base
+    // tiles + one crossing ring per warp + alignment slack of the dynamic base
+    const int qf = dim == 3 ? QFields<3>::n : QFields<2>::n;
+    return smem_plan(ebs, js).bytes + (size_t)(threads / 32) * qf * WQ * sizeof(double) + 128;
 }
 
 template <int DIM, int ORDER>
 static cudaError_t launch_particles_t(const LaunchCfg& cfg, size_t smem, const SchedDev* sched,
                                       SimDev* sims, cudaStream_t st) {
-    pic_particle_kernel<DIM, ORDER><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    if (cfg.minb == 2) pic_particle_kernel<DIM, ORDER, 2><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    else pic_particle_kernel<DIM, ORDER, 1><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
     return cudaGetLastError();
-}
-
-int pic_particle_occupancy(int dim, int order, int threads, size_t smem) {
-    int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    if (dim == 3 && order == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<3, 1>, threads, smem);
-    else if (dim == 3 && order == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<3, 2>, threads, smem);
-    else if (dim == 2 && order == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<2, 1>, threads, smem);
-    else if (dim == 2 && order == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<2, 2>, threads, smem);
-    return e == cudaSuccess ? n : 0;
-}
-
-cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
-    const int b = (int)smem;
-    if (dim == 3 && order == 1)
-        return cudaFuncSetAttribute(pic_particle_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (dim == 3 && order == 2)
-        return cudaFuncSetAttribute(pic_particle_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (dim == 2 && order == 1)
-        return cudaFuncSetAttribute(pic_particle_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (dim == 2 && order == 2)
-        return cudaFuncSetAttribute(pic_particle_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
@@ -977,6 +1052,41 @@ cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_
     if (dim == 3 && order == 2) return launch_particles_t<3, 2>(cfg, smem, sched, sims, st);
     if (dim == 2 && order == 1) return launch_particles_t<2, 1>(cfg, smem, sched, sims, st);
     if (dim == 2 && order == 2) return launch_particles_t<2, 2>(cfg, smem, sched, sims, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int DIM, int ORDER>
+static cudaError_t prepare_t(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <int DIM, int ORDER>
+static int occupancy_t(int minb, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e = minb == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, pic_particle_kernel<DIM, ORDER, 2>, threads, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, pic_particle_kernel<DIM, ORDER, 1>, threads, smem);
+    return e == cudaSuccess ? n : 0;
+}
+
+int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem) {
+    if (dim == 3 && order == 1) return occupancy_t<3, 1>(minb, threads, smem);
+    if (dim == 3 && order == 2) return occupancy_t<3, 2>(minb, threads, smem);
+    if (dim == 2 && order == 1) return occupancy_t<2, 1>(minb, threads, smem);
+    if (dim == 2 && order == 2) return occupancy_t<2, 2>(minb, threads, smem);
+    return 0;
+}
+
+cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
+    if (dim == 3 && order == 1) return prepare_t<3, 1>(smem);
+    if (dim == 3 && order == 2) return prepare_t<3, 2>(smem);
+    if (dim == 2 && order == 1) return prepare_t<2, 1>(smem);
+    if (dim == 2 && order == 2) return prepare_t<2, 2>(smem);
     return cudaErrorInvalidValue;
 }
 

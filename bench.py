@@ -168,11 +168,14 @@ def run_ours(args, rank, world):
 
     # ---- balanced (the paper's dynamic load balancing, on the SMs)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
-    if args.threads or args.ctas_per_sm:
-        sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
     sim.step(1)                                      # measure per-box clock costs once
     sim.rebalance(**dict(lbkw, theta=0.0))           # initial cost-driven mapping
     sim.set_lb_params(**lbkw)
+    if args.threads or args.ctas_per_sm:
+        sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+        tuned = sim.get_launch()
+    else:
+        tuned = sim.autotune(steps_per_candidate=2)  # threads, CTAs/SM, units per worker
     sim.step(args.warmup)
     with ClockSampler(dev) as cs:
         ms_bal = timed(sim, args.steps)
@@ -281,7 +284,7 @@ def run_ours(args, rank, world):
         "fdtd_cell_updates_per_s": ncells / (st["ms_fields"] / max(st["steps"], 1) / 1e3),
         "lb": {"e_old": lb["e_old"], "e_new": lb["e_new"], "n_units": lb["n_units"],
                "predicted_speedup_sec4": lb["predicted_speedup"]},
-        "config": dict(workload_desc(wl), sched=args.sched),
+        "config": dict(workload_desc(wl), sched=args.sched, launch=tuned),
     }
 
 

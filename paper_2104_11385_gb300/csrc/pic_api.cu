@@ -1042,10 +1042,11 @@ pic_status pic_set_launch(pic_sim* s, const pic_launch_cfg* cfg) {
         if (cfg->ctas_per_sm > 4) return fail(s, PIC_EINVAL, "ctas_per_sm must be 1..4");
         s->ctas_per_sm = cfg->ctas_per_sm;
     }
+    const int old_split = s->split;
     if (cfg->split > 0) s->split = cfg->split;
-    int old = s->ctas;
+    const int old = s->ctas;
     TRY(configure_launch(s));
-    if (s->ctas != old) TRY(replan(s));
+    if (s->ctas != old || s->split != old_split) TRY(replan(s));
     return PIC_OK;
 }
 
@@ -1061,8 +1062,11 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     TRY(check(s));
     if (steps_per_candidate < 1) return fail(s, PIC_EINVAL, "steps_per_candidate must be >= 1");
     TRY(ensure_ready(s));
+    // candidates: threads per CTA x resident CTAs per SM (register budget of the
+    // kernel variant) x work units per worker (how finely heavy boxes are cut)
     const int threads_c[2] = {128, 256};
     const int cps_c[2] = {1, 2};
+    const int split_c[3] = {4, 16, 64};
     float best_ms = 1e30f;
     pic_launch_cfg best_cfg{s->threads, s->ctas_per_sm, s->split};
     cudaEvent_t a, b;
@@ -1070,23 +1074,26 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     CU(s, cudaEventCreate(&b));
     const bool prof = s->profiling;
     s->profiling = false;
+    const bool splits = s->lb_set && s->lb.mode != PIC_LB_NONE;
     for (int t : threads_c)
-        for (int c : cps_c) {
-            pic_launch_cfg cfg{t, c, 0};
-            TRY(pic_set_launch(s, &cfg));
-            if (s->ctas / s->nsm != c) continue;  // not resident: skip
-            TRY(pic_step(s, 1));
-            CU(s, cudaEventRecord(a, s->stream));
-            TRY(pic_step(s, steps_per_candidate));
-            CU(s, cudaEventRecord(b, s->stream));
-            CU(s, cudaEventSynchronize(b));
-            float ms = 0;
-            cudaEventElapsedTime(&ms, a, b);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_cfg = pic_launch_cfg{t, c, s->split};
+        for (int c : cps_c)
+            for (int sp : split_c) {
+                if (!splits && sp != split_c[1]) continue;  // no cut boxes without balancing
+                pic_launch_cfg cfg{t, c, sp};
+                TRY(pic_set_launch(s, &cfg));
+                if (s->ctas / s->nsm != c) continue;  // not resident: skip
+                TRY(pic_step(s, 1));
+                CU(s, cudaEventRecord(a, s->stream));
+                TRY(pic_step(s, steps_per_candidate));
+                CU(s, cudaEventRecord(b, s->stream));
+                CU(s, cudaEventSynchronize(b));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_cfg = pic_launch_cfg{t, c, sp};
+                }
             }
-        }
     s->profiling = prof;
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -54,9 +54,31 @@ def parse():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
+    ap.add_argument("--no-cost-arms", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--server-requests", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
+
+
+def _jsonable(o):
+    """numpy scalars and arrays in the JSON line"""
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    return str(o)
+
+
+def max_over_ranks(value, world):
+    """Maximum of a per-rank float over all ranks (the slowest rank sets the
+    job's time); plain value when running alone."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def make_workload(name, scale, seed_offset=0):
@@ -159,12 +181,7 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), world)
 
     # ---- balanced (the paper's dynamic load balancing, on the SMs)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
@@ -177,15 +194,16 @@ def run_ours(args, rank, world):
     else:
         tuned = sim.autotune(steps_per_candidate=2)  # threads, CTAs/SM, units per worker
     sim.step(args.warmup)
+    nlog0 = len(sim.lb_log())
     with ClockSampler(dev) as cs:
         ms_bal = timed(sim, args.steps)
     clocks = cs.summary()
+    lb_timed = sim.lb_log()[nlog0:]  # the load-balancing calls made inside the timed steps
     # kernel-level timing (CUDA events on the library's stream around each launch)
     sim.set_profiling(True)
     sim.step(min(args.steps, 10))
     st = sim.stats()
     sim.set_profiling(False)
-    lb = sim.rebalance(**lbkw)
     kernels_per_step = st["launches"] / max(st["steps"], 1)
     sim.close()
     del sim
@@ -203,6 +221,22 @@ def run_ours(args, rank, world):
     sim.close()
     del sim
     torch.cuda.empty_cache()
+
+    # ---- the paper's cost strategies side by side (same schedule, same tuning)
+    cost_arms = {"device_clock": nparts * args.steps * world / (ms_bal / 1e3)}
+    if not args.no_cost_arms:
+        for name, cst in (("heuristic", pic.COST_HEURISTIC), ("kernel_time", pic.COST_KERNEL_TIME)):
+            ckw = dict(lbkw, cost=cst)
+            sim = pic.from_workload(wl, stream=stream.cuda_stream)
+            sim.step(1)
+            sim.rebalance(**dict(ckw, theta=0.0))
+            sim.set_lb_params(**ckw)
+            sim.set_launch(**{k: tuned[k] for k in ("threads", "ctas_per_sm", "split")})
+            sim.step(args.warmup)
+            cost_arms[name] = nparts * args.steps * world / (timed(sim, args.steps) / 1e3)
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
 
     # ---- static box order (no load balancing: the fixed starting mapping)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
@@ -240,11 +274,7 @@ def run_ours(args, rank, world):
         t1 = time.perf_counter()
         d2h = out_e.numel() * 8 + costs.nbytes + npb.nbytes
         sim.close()
-        secs = t1 - t0
-        if world > 1:
-            t = torch.tensor([secs], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            secs = float(t.item())
+        secs = max_over_ranks(t1 - t0, world)
         e2e = {"value": nparts * (args.steps + 1) * world / secs, "unit": "particle-updates/s",
                "h2d_bytes_per_step": int(h2d / (args.steps + 1)),
                "d2h_bytes_per_step": int(d2h / (args.steps + 1)),
@@ -278,14 +308,74 @@ def run_ours(args, rank, world):
                          "what": "mode NONE: one unit per box, fixed equal-count Morton mapping, per-worker lists"},
         "other_schedule": {"sched": other, "value": nparts * args.steps * world / (ms_other / 1e3),
                            "ms_per_step": ms_other / args.steps},
+        "cost_strategies": cost_arms,
         "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
         "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
                               "sort": st["ms_sort"] / max(st["steps"], 1)},
         "fdtd_cell_updates_per_s": ncells / (st["ms_fields"] / max(st["steps"], 1) / 1e3),
-        "lb": {"e_old": lb["e_old"], "e_new": lb["e_new"], "n_units": lb["n_units"],
-               "predicted_speedup_sec4": lb["predicted_speedup"]},
+        "lb": {"calls_in_timed_steps": len(lb_timed),
+               "adopted": sum(1 for r in lb_timed if r["adopted"]),
+               "last": lb_timed[-1] if lb_timed else None},
         "config": dict(workload_desc(wl), sched=args.sched, launch=tuned),
     }
+
+
+def run_c3(args, steps=10):
+    """Batched uneven boxes: 4096 boxes of 16^3 cells (256^3), box particle
+    counts round(exp(N(ln 2000, 2^2))) (~60M particles), quadratic shape, one
+    persistent autotuned launch per step; static box order against
+    device-clock, kernel-time and heuristic costs, and how well each cost
+    tracks the particle count."""
+    import numpy as np
+    import torch
+    from scipy.stats import spearmanr
+    import paper_2104_11385_gb300 as pic
+    from paper_2104_11385_gb300 import workloads as W
+    wl = W.lognormal(seed=3)
+    nparts = sum(len(s["x"]) for s in wl["species"])
+    stream = torch.cuda.Stream()
+    out = {"workload": "lognormal 16^3 boxes of 16^3 cells, quadratic", "particles": nparts,
+           "max_box_particles": int(wl["box_counts"].max()), "steps": steps}
+
+    def timed(sim, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    sim.step(2)
+    ms = timed(sim, steps)
+    out["static_order"] = nparts * steps / (ms / 1e3)
+    sim.close()
+    tuned = None
+    for name, cst in (("device_clock", pic.COST_DEVICE_CLOCK), ("kernel_time", pic.COST_KERNEL_TIME),
+                      ("heuristic", pic.COST_HEURISTIC)):
+        kw = dict(mode=pic.LB_DYNAMIC, interval=10, theta=0.10, policy=pic.POLICY_KNAPSACK, cost=cst,
+                  sched=pic.SCHED_QUEUE)
+        sim = pic.from_workload(wl, stream=stream.cuda_stream)
+        sim.step(1)
+        if name == "device_clock":
+            clk, npb = sim.box_costs(pic.COST_DEVICE_CLOCK)
+            kt, _ = sim.box_costs(pic.COST_KERNEL_TIME)
+            out["spearman_device_clock_vs_np"] = float(spearmanr(clk, npb).correlation)
+            out["spearman_kernel_time_vs_np"] = float(spearmanr(kt, npb).correlation)
+        sim.rebalance(**dict(kw, theta=0.0))
+        sim.set_lb_params(**kw)
+        if tuned is None:
+            tuned = sim.autotune(steps_per_candidate=1)
+        else:
+            sim.set_launch(**tuned)
+        sim.step(2)
+        ms = timed(sim, steps)
+        out[name] = nparts * steps / (ms / 1e3)
+        sim.close()
+    out["launch"] = tuned
+    out["speedup_balanced_over_static"] = out["device_clock"] / out["static_order"]
+    return out
 
 
 def run_server(args, seed=4):
@@ -414,6 +504,9 @@ def main():
     server = None
     if rank == 0 and not args.no_server:
         server = run_server(args)
+    c3 = None
+    if rank == 0 and not args.no_c3:
+        c3 = run_c3(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=6)
@@ -427,10 +520,11 @@ def main():
                 "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
                 "static_order": res["static_order"], "other_schedule": res["other_schedule"],
+                "cost_strategies": res["cost_strategies"], "batched_uneven_boxes": c3,
                 "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
                 "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"], "server": server}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_jsonable), flush=True)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

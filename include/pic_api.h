@@ -120,7 +120,7 @@ pic_status pic_set_field(pic_sim* sim, int comp, const double* data, int on_devi
 
 /* ---- load balancing (Sec. 2.2) ------------------------------------------- */
 enum { PIC_POLICY_KNAPSACK = 0, PIC_POLICY_SFC = 1 };
-enum { PIC_COST_HEURISTIC = 0, PIC_COST_DEVICE_CLOCK = 1 };
+enum { PIC_COST_HEURISTIC = 0, PIC_COST_DEVICE_CLOCK = 1, PIC_COST_KERNEL_TIME = 2 };
 enum { PIC_LB_NONE = 0, PIC_LB_STATIC = 1, PIC_LB_DYNAMIC = 2 };
 enum { PIC_SCHED_LISTS = 0, PIC_SCHED_QUEUE = 1 };
 
@@ -132,8 +132,11 @@ enum { PIC_SCHED_LISTS = 0, PIC_SCHED_QUEUE = 1 };
  *   theta       required relative improvement of E to adopt a new mapping
  *               (E_new >= (1 + theta) E_old; Sec. 3.2 uses 0.10).
  *   policy      knapsack or Morton space-filling curve.
- *   cost        heuristic (w_p Np + w_c Nc per box) or device clock (summed
- *               per-thread clock64 of the particle kernel, per box).
+ *   cost        heuristic (w_p Np + w_c Nc per box), device clock (summed
+ *               per-thread clock64 of the particle kernel, per box; the
+ *               paper's GPU-clock strategy), or kernel time (summed
+ *               %globaltimer span of the box's work units: the in-kernel
+ *               analog of the paper's CUPTI kernel duration, without CUPTI).
  *   w_p, w_c    heuristic weights (Sec. 3.3 footnotes: 0.75/0.25 knapsack,
  *               0.02/0.98 SFC).
  *   cap_factor  knapsack cap on units per worker, times the average (1.5).
@@ -181,7 +184,8 @@ pic_status pic_sync(pic_sim* sim);
 /* Per-box cost (Sec. 2.2 strategies).  strategy HEURISTIC: w_p*Np + w_c*Nc
  * with the weights of the last pic_set_lb_params (0.75/0.25 by default);
  * DEVICE_CLOCK: summed thread clock cycles of the particle kernel since the
- * last rebalance (or since the start).  costs_out: host, nboxes doubles;
+ * last rebalance (or since the start); KERNEL_TIME: summed nanoseconds
+ * (%globaltimer) of the box's work units over the same window.  costs_out: host, nboxes doubles;
  * np_out: host, nboxes int64 particle counts (nullable).  Box index
  * (bz*nby + by)*nbx + bx.  Synchronises the stream. */
 pic_status pic_get_box_costs(pic_sim* sim, int strategy, double* costs_out, int64_t* np_out);
@@ -193,6 +197,11 @@ pic_status pic_get_box_costs(pic_sim* sim, int strategy, double* costs_out, int6
  * Resets the accumulated device-clock costs.  Synchronises the stream. */
 pic_status pic_rebalance(pic_sim* sim, const pic_lb_params* params, pic_lb_result* out,
                          int32_t* assign_out);
+
+/* Log of the load-balancing calls made so far (by pic_step at its intervals
+ * and by pic_rebalance), oldest first: copies min(max, n_total) entries into
+ * out (host, nullable when max == 0) and the total count into *n_total. */
+pic_status pic_get_lb_log(pic_sim* sim, pic_lb_result* out, int64_t max, int64_t* n_total);
 
 /* Pure host function, the bit-exact test surface of the balancer (Sec. 2.2):
  * maps nboxes boxes with the given costs to n_workers workers.

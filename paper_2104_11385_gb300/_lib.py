@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA"
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 BIN_NOALLOC_MAX_BOXES = 1 << 20  # PIC_BIN_NOALLOC_MAX_BOXES of include/pic_noalloc.h
 POLICY_KNAPSACK, POLICY_SFC = 0, 1
-COST_HEURISTIC, COST_DEVICE_CLOCK = 0, 1
+COST_HEURISTIC, COST_DEVICE_CLOCK, COST_KERNEL_TIME = 0, 1, 2
 LB_NONE, LB_STATIC, LB_DYNAMIC = 0, 1, 2
 SCHED_LISTS, SCHED_QUEUE = 0, 1
 
@@ -99,6 +99,7 @@ SIGNATURES = [
     ("pic_sync", _int, [_vp]),
     ("pic_get_box_costs", _int, [_vp, _int, _pd, _pi64]),
     ("pic_rebalance", _int, [_vp, ctypes.POINTER(LBParams), ctypes.POINTER(LBResult), _pi32]),
+    ("pic_get_lb_log", _int, [_vp, ctypes.POINTER(LBResult), _i64, _pi64]),
     ("pic_balance_compute", _int, [_pd, _i64, _pi32, _int, _int, _int, _d, _pi32, _pd]),
     ("pic_lb_efficiency", _int, [_pd, _pi32, _i64, _int, _pd]),
     ("pic_read_fields", _int, [_vp, _int, _vp, _int]),

@@ -322,10 +322,10 @@ pic_status box_costs(pic_sim* s, int strategy, double w_p, double w_c, std::vect
     TRY(box_counts(s, np));
     const int64_t nb = s->h.nboxes;
     costs.assign(nb, 0.0);
-    if (strategy == PIC_COST_DEVICE_CLOCK) {
+    if (strategy == PIC_COST_DEVICE_CLOCK || strategy == PIC_COST_KERNEL_TIME) {
         std::vector<uint64_t> clk(nb);
-        CU(s, cudaMemcpyAsync(clk.data(), s->h.cost_clock, nb * sizeof(uint64_t),
-                              cudaMemcpyDeviceToHost, s->stream));
+        CU(s, cudaMemcpyAsync(clk.data(), strategy == PIC_COST_DEVICE_CLOCK ? s->h.cost_clock : s->h.cost_time,
+                              nb * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
         CU(s, cudaStreamSynchronize(s->stream));
         for (int64_t b = 0; b < nb; ++b) costs[b] = (double)clk[b];
     } else {
@@ -355,7 +355,7 @@ pic_status validate_lb(pic_sim* s, const pic_lb_params* p) {
     if (!p) return fail(s, PIC_EINVAL, "null load-balancing parameters");
     if (p->mode < PIC_LB_NONE || p->mode > PIC_LB_DYNAMIC || p->interval < 1 || !(p->theta >= 0.0) ||
         (p->policy != PIC_POLICY_KNAPSACK && p->policy != PIC_POLICY_SFC) ||
-        (p->cost != PIC_COST_HEURISTIC && p->cost != PIC_COST_DEVICE_CLOCK) ||
+        (p->cost != PIC_COST_HEURISTIC && p->cost != PIC_COST_DEVICE_CLOCK && p->cost != PIC_COST_KERNEL_TIME) ||
         !(p->cap_factor > 0.0) || p->n_workers < 0 || p->split < 0 ||
         (p->sched != PIC_SCHED_LISTS && p->sched != PIC_SCHED_QUEUE) || !std::isfinite(p->w_p) ||
         !std::isfinite(p->w_c))
@@ -403,6 +403,7 @@ pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_re
     s->last_costs = costs;
     s->last_np = np;
     CU(s, cudaMemsetAsync(s->h.cost_clock, 0, nb * sizeof(uint64_t), s->stream));
+    CU(s, cudaMemsetAsync(s->h.cost_time, 0, nb * sizeof(uint64_t), s->stream));
     pic_lb_result r;
     r.e_old = e_old;
     r.e_new = e_new;
@@ -542,7 +543,7 @@ int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, i
         ntiles *= nb * (T > 0 ? g->box[a] / T : 1);
     }
     auto r = [](int64_t n, int64_t sz) { return std::max<int64_t>(n, 1) * sz; };
-    int64_t b = r(pvol * PIC_NCOMP, 8) + r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) +
+    int64_t b = r(pvol * PIC_NCOMP, 8) + 2 * r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) +
                 (int64_t)sizeof(SchedDev) + r(8193, 4) + r(8192, 4) + r(2, 4) + r(4, 8) + r(nboxes, 8);
     for (int i = 0; i < nsp; ++i) {
         const int64_t cap = std::max<int64_t>(np[i], 1);
@@ -657,7 +658,8 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     }
     for (int c = 0; c < PIC_NCOMP; ++c) h.F[c] = fields + (int64_t)c * pvol;
     if (cudaMemset(fields, 0, (size_t)pvol * PIC_NCOMP * sizeof(double)) != cudaSuccess ||
-        (st = dalloc(s, &h.cost_clock, h.nboxes)) != PIC_OK || (st = dalloc(s, &h.step, 1)) != PIC_OK ||
+        (st = dalloc(s, &h.cost_clock, h.nboxes)) != PIC_OK || (st = dalloc(s, &h.cost_time, h.nboxes)) != PIC_OK ||
+        (st = dalloc(s, &h.step, 1)) != PIC_OK ||
         (st = dalloc(s, &h.err, 1)) != PIC_OK || (st = dalloc(s, &s->d, 1)) != PIC_OK ||
         (st = dalloc(s, &s->ds, 1)) != PIC_OK || (st = dalloc(s, &s->hs.list_off, 8193)) != PIC_OK ||
         (st = dalloc(s, &s->hs.head, 8192)) != PIC_OK || (st = dalloc(s, &s->hs.meta, 2)) != PIC_OK ||
@@ -667,6 +669,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         return st == PIC_OK ? PIC_ECUDA : st;
     }
     cudaMemset(h.cost_clock, 0, h.nboxes * sizeof(uint64_t));
+    cudaMemset(h.cost_time, 0, h.nboxes * sizeof(uint64_t));
     cudaMemset(h.step, 0, sizeof(int64_t));
     cudaMemset(h.err, 0, sizeof(int32_t));
     cudaMemset(s->hs.head, 0, 8192 * sizeof(int32_t));
@@ -891,7 +894,8 @@ pic_status pic_sync(pic_sim* s) {
 
 pic_status pic_get_box_costs(pic_sim* s, int strategy, double* costs_out, int64_t* np_out) {
     TRY(check(s));
-    if (!costs_out || (strategy != PIC_COST_HEURISTIC && strategy != PIC_COST_DEVICE_CLOCK))
+    if (!costs_out || (strategy != PIC_COST_HEURISTIC && strategy != PIC_COST_DEVICE_CLOCK &&
+                       strategy != PIC_COST_KERNEL_TIME))
         return fail(s, PIC_EINVAL, "bad cost request");
     if (!s->stepped) TRY(upload_sim(s));
     TRY(sync_and_check(s));
@@ -922,6 +926,14 @@ pic_status pic_rebalance(pic_sim* s, const pic_lb_params* params, pic_lb_result*
             if (P.units[i].chunk == 0) assign_out[P.units[i].box] = P.unit_worker[i];
     }
     return check_device_error(s);
+}
+
+pic_status pic_get_lb_log(pic_sim* s, pic_lb_result* out, int64_t max, int64_t* n_total) {
+    if (!s || !n_total || max < 0 || (max > 0 && !out)) return fail(s, PIC_EINVAL, "bad log arguments");
+    const int64_t n = (int64_t)s->lb_log.size();
+    for (int64_t i = 0; i < std::min(n, max); ++i) out[i] = s->lb_log[i];
+    *n_total = n;
+    return PIC_OK;
 }
 
 pic_status pic_balance_compute(const double* costs, int64_t nboxes, const int32_t* box_ijk,

@@ -75,7 +75,8 @@ struct SimDev {
     double jfac[3];       // -1/(dA_perp dt) for the prefix currents (3D); 2D see kernel
     double jyfac2d;       // 1/(dx dz) for the 2D out-of-plane current
     double* F[PIC_NCOMP]; // padded field arrays
-    uint64_t* cost_clock; // [nboxes]
+    uint64_t* cost_clock; // [nboxes] summed thread clock64 cycles (device-clock cost)
+    uint64_t* cost_time;  // [nboxes] summed %globaltimer ns of the box's units (kernel-time cost)
     int64_t* step;        // device step counter
     int32_t* err;         // device error word (shared with the schedule)
     LaserDev las;

@@ -778,6 +778,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         if (u < 0) break;
         const UnitDev unit = sd->units[u];
         const SimDev& S = sims[unit.sim];
+        const uint64_t t_unit0 = threadIdx.x == 0 ? globaltimer() : 0ull;
         const SmemPlan P = smem_plan(S.ebs, S.js);
         double* sEB = smem;
         double* sJ = smem + 6 * P.eb_stride;
@@ -868,6 +869,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         if (threadIdx.x == 0) {
             if (s_cost) atomicAdd((unsigned long long*)(S.cost_clock + unit.box), s_cost);
             s_cost = 0ull;
+            // kernel-time cost: wall span of the unit on this CTA (ns)
+            atomicAdd((unsigned long long*)(S.cost_time + unit.box),
+                      (unsigned long long)(globaltimer() - t_unit0));
         }
     }
     if (cur.t >= 0) {

@@ -142,6 +142,14 @@ class Simulation:
         return {"e_old": r.e_old, "e_new": r.e_new, "adopted": bool(r.adopted), "n_units": r.n_units,
                 "predicted_speedup": r.predicted_speedup, "assign": a}
 
+    def lb_log(self) -> list:
+        n = ctypes.c_int64()
+        self._check(self._lib.pic_get_lb_log(self._h, None, 0, ctypes.byref(n)))
+        buf = (L.LBResult * max(n.value, 1))()
+        self._check(self._lib.pic_get_lb_log(self._h, buf, n.value, ctypes.byref(n)))
+        return [{"e_old": r.e_old, "e_new": r.e_new, "adopted": bool(r.adopted), "n_units": r.n_units,
+                 "predicted_speedup": r.predicted_speedup} for r in buf[:n.value]]
+
     def read_field(self, comp, out=None):
         if out is None:
             out = np.empty(self.ncells_total, np.float64)

@@ -119,6 +119,9 @@ def test_lognormal_uneven_boxes_parity_with_balancing():
     sim.step(10)
     ref.step(10)
     compare(sim, ref, wl)
+    log = sim.lb_log()
+    assert len(log) == 3  # steps 3, 6, 9
+    assert all(0.0 < r["e_new"] <= 1.0 and r["adopted"] for r in log)  # theta 0: always adopted
 
 
 @pytest.mark.parametrize("sched,policy,cost", [
@@ -155,6 +158,7 @@ def test_box_counts_and_clock_costs():
     sim.step(3)
     ref.step(3)
     clk, np_gpu = sim.box_costs(pic.COST_DEVICE_CLOCK)
+    ktime, _ = sim.box_costs(pic.COST_KERNEL_TIME)
     heur, _ = sim.box_costs(pic.COST_HEURISTIC)
     assert np.array_equal(np_gpu, ref.box_counts(wl["box"]))
     assert np.all(clk[np_gpu > 0] > 0)
@@ -164,6 +168,9 @@ def test_box_counts_and_clock_costs():
     from scipy.stats import spearmanr
     rho = spearmanr(clk, np_gpu).correlation
     assert rho > 0.9, rho
+    # the kernel-time cost (summed unit durations) tracks it too
+    assert np.all(ktime[np_gpu > 0] > 0)
+    assert spearmanr(ktime, np_gpu).correlation > 0.8
 
 
 def test_empty_species_and_empty_run():

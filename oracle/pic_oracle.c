@@ -68,12 +68,18 @@ static int64_t idx3(const orc_sim* s, int64_t i, int64_t j, int64_t k) {
 }
 
 /* B-spline shape S(dist): order 1 is the hat 1-|d| on |d|<1; order 2 is
- * 3/4-d^2 on |d|<1/2 and (3/2-|d|)^2/2 on 1/2<=|d|<3/2. */
+ * 3/4-d^2 on |d|<1/2 and (3/2-|d|)^2/2 on 1/2<=|d|<3/2; order 3 (the paper's
+ * choice, Sec. 3.1) is 2/3-d^2+|d|^3/2 on |d|<1 and (2-|d|)^3/6 on 1<=|d|<2. */
 double orc_shape(int order, double dist) {
     double a = fabs(dist);
     if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
-    if (a < 0.5) return 0.75 - a * a;
-    if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+    if (order == 2) {
+        if (a < 0.5) return 0.75 - a * a;
+        if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+        return 0.0;
+    }
+    if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+    if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
     return 0.0;
 }
 
@@ -81,13 +87,14 @@ double orc_shape(int order, double dist) {
  * (xi in cell units, measured from the component's own grid origin). */
 static int64_t support_start(int order, double xi) {
     if (order == 1) return (int64_t)floor(xi);
-    return (int64_t)floor(xi + 0.5) - 1;
+    if (order == 2) return (int64_t)floor(xi + 0.5) - 1;
+    return (int64_t)floor(xi) - 1;
 }
 
 orc_sim* orc_create(int dim, const int64_t n[3], const double d[3], double dt,
                     int order, int absorb_cells) {
     if (dim != 2 && dim != 3) return NULL;
-    if (order != 1 && order != 2) return NULL;
+    if (order < 1 || order > 3) return NULL;
     if (n[0] < 1 || n[1] < 1 || n[2] < 1) return NULL;
     if (dim == 2 && n[1] != 1) return NULL;
     if (absorb_cells < 0 || 2 * (int64_t)absorb_cells >= n[2]) return NULL;
@@ -186,7 +193,7 @@ static double gather_comp(const orc_sim* s, int comp, const double X[3]) {
     int o = s->order;
     int np1 = o + 1;
     int64_t base[3];
-    double wt[3][3];
+    double wt[3][4];
     for (int a = 0; a < 3; a++) {
         if (a == 1 && s->dim == 2) { base[a] = 0; wt[a][0] = 1.0; continue; }
         double xi = X[a] - STAG[comp][a];
@@ -240,11 +247,12 @@ void orc_boris(double q, double m, double dt, const double eb[6], double u[3]) {
 /* W (Esirkepov 2001, Eq. 31 in 3D; the 2D form with the out-of-plane    */
 /* current) are prefix-summed along their own direction.                 */
 /* ------------------------------------------------------------------ */
-#define WMAX 5
+#define WMAX 6
 
 static int64_t window_start(int order, double X0) {
     if (order == 1) return (int64_t)floor(X0) - 1;
-    return (int64_t)floor(X0 + 0.5) - 2;
+    if (order == 2) return (int64_t)floor(X0 + 0.5) - 2;
+    return (int64_t)floor(X0) - 2;
 }
 
 static void node_shapes(int order, double X0, double X1, int64_t base, int L,
@@ -510,7 +518,7 @@ int orc_deposit_rho(const orc_sim* s, double* rho) {
             double X[3] = {sp->x[p] / s->d[0], s->dim == 3 ? sp->y[p] / s->d[1] : 0.0,
                            sp->z[p] / s->d[2]};
             int64_t b[3];
-            double wt[3][3];
+            double wt[3][4];
             for (int a = 0; a < 3; a++) {
                 if (a == 1 && s->dim == 2) { b[a] = 0; wt[a][0] = 1.0; continue; }
                 b[a] = support_start(o, X[a]);

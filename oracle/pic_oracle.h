@@ -37,7 +37,7 @@ typedef struct orc_sim orc_sim;
 enum { ORC_EX = 0, ORC_EY, ORC_EZ, ORC_BX, ORC_BY, ORC_BZ, ORC_JX, ORC_JY, ORC_JZ };
 
 /* dim: 2 or 3; n: cells (nx, ny, nz) with ny == 1 when dim == 2;
- * d: cell sizes; dt: time step; order: shape order 1 or 2;
+ * d: cell sizes; dt: time step; order: shape order 1, 2 or 3;
  * absorb_cells: 0 = fully periodic; > 0 = width (in z cells) of the damping
  * layers at both z ends, where particles are removed.  Returns NULL on bad input. */
 orc_sim* orc_create(int dim, const int64_t n[3], const double d[3], double dt,

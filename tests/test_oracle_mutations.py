@@ -32,7 +32,15 @@ MUTATIONS = [
     ("esirkepov 2D: out-of-plane 1/3 term", "DSx[l] * DSz[n] / 3.0;", "DSx[l] * DSz[n] / 2.0;"),
     ("esirkepov 2D: Jz weight", "acc += DSz[n] * (S0x[l] + 0.5 * DSx[l]);", "acc += DSz[n] * (S0x[l] + DSx[l]);"),
     ("esirkepov: quadratic window from floor(x)", "return (int64_t)floor(X0 + 0.5) - 2;",
-     "return (int64_t)floor(X0) - 2;"),
+     "return (int64_t)floor(X0) - 2;\n    if (0) return 0;"),
+    ("esirkepov: cubic window one node short", "    return (int64_t)floor(X0) - 2;\n}",
+     "    return (int64_t)floor(X0) - 1;\n}"),
+    ("shape: cubic outer piece", "if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;",
+     "if (a < 2.0) return (2.0 - a) * (2.0 - a) / 6.0;"),
+    ("shape: cubic inner piece sign", "if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;",
+     "if (a < 1.0) return 2.0 / 3.0 - a * a - 0.5 * a * a * a;"),
+    ("gather: cubic support from the nearest node", "    return (int64_t)floor(xi) - 1;\n}",
+     "    return (int64_t)floor(xi + 0.5) - 1;\n}"),
     ("ampere: J sign", "F(ORC_EX, i, j, k) += dt * (cBx - F(ORC_JX, i, j, k));",
      "F(ORC_EX, i, j, k) += dt * (cBx + F(ORC_JX, i, j, k));"),
     ("faraday: backward instead of forward difference",

@@ -25,8 +25,12 @@ def test_shape_values_and_partition_of_unity():
     assert orc.shape(1, 0.0) == 1.0 and orc.shape(1, 0.25) == 0.75 and orc.shape(1, 1.0) == 0.0
     assert orc.shape(2, 0.0) == 0.75 and orc.shape(2, 0.5) == 0.5
     assert orc.shape(2, 1.0) == 0.125 and orc.shape(2, 1.5) == 0.0
+    assert orc.shape(3, 0.0) == pytest.approx(2 / 3, abs=1e-16) and orc.shape(3, 1.0) == pytest.approx(1 / 6, abs=1e-16)
+    assert orc.shape(3, 2.0) == 0.0 and orc.shape(3, 1.5) == pytest.approx(1 / 48, abs=1e-16)
+    # the cubic B-spline is the hat convolved with the hat: S3(0.5) = 23/48
+    assert orc.shape(3, 0.5) == pytest.approx(23 / 48, abs=1e-16)
     rng = np.random.default_rng(0)
-    for order in (1, 2):
+    for order in (1, 2, 3):
         for x in rng.uniform(-3, 3, 50):
             nodes = np.arange(math.floor(x) - 3, math.floor(x) + 4)
             vals = [orc.shape(order, x - k) for k in nodes]
@@ -39,7 +43,7 @@ def test_shape_values_and_partition_of_unity():
 STAG = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
 
 
-@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (3, 3), (2, 1), (2, 2), (2, 3)])
 def test_gather_reproduces_linear_fields(dim, order):
     """Linear and quadratic B-splines interpolate affine fields exactly, so any
     error in a component's staggering offset shows up as a b*dx/2 bias."""
@@ -196,7 +200,7 @@ def test_yee_vacuum_dispersion(dim):
 
 
 # ------------------------------------------------------- plasma frequency ---
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_cold_plasma_oscillation_leapfrog_frequency(order):
     """Uniform cold electrons (lattice loaded) drifting with u0 over fixed
     ions: the k = 0 mode is the leapfrog oscillator with
@@ -243,7 +247,7 @@ def _div_nodes(dim, n, d, Fx, Fy, Fz):
     return div
 
 
-@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (3, 3), (2, 1), (2, 2), (2, 3)])
 def test_esirkepov_discrete_continuity(dim, order):
     """(rho^{n+1} - rho^n)/dt + div J^{n+1/2} = 0 at every node (Esirkepov
     2001), with rho deposited by S at the nodes; fast particles so that many
@@ -270,7 +274,7 @@ def test_esirkepov_discrete_continuity(dim, order):
     assert np.abs(J[0]).max() > 1e-3 * scale * d[0]  # currents are not trivially zero
 
 
-@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (2, 2)])
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (3, 3), (2, 2), (2, 3)])
 def test_gauss_law_residual_preserved(dim, order):
     """Charge-conserving deposit + Yee: div E - rho changes by roundoff only."""
     n = (6, 6 if dim == 3 else 1, 6)

@@ -61,7 +61,8 @@ enum {
  *   dt           time step; <= 0 selects cfl * Courant limit
  *                (dt = cfl / sqrt(sum 1/dx_i^2) over the active directions).
  *   cfl          used only when dt <= 0.
- *   shape_order  1 (linear) or 2 (quadratic) B-spline particle shape.
+ *   shape_order  1 (linear), 2 (quadratic) or 3 (cubic, the paper's choice in
+ *                Sec. 3.1) B-spline particle shape.
  *   absorb_cells 0: periodic in every direction.  > 0: x and y periodic; at
  *                both z ends a damping layer of this many cells scales E and B
  *                each step, and particles entering it are removed.

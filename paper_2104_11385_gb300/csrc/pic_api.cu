@@ -535,7 +535,7 @@ int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, i
     int64_t pvol = 1, nboxes = 1, ntiles = 1;
     for (int a = 0; a < 3; ++a) {
         const bool act = !(g->dim == 2 && a == 1);
-        const int gw = act ? (a == 0 ? PIC_GX : PIC_G) : 0;
+        const int gw = act ? (a == 0 ? (g->shape_order == 3 ? PIC_GX + 1 : PIC_GX) : PIC_G) : 0;
         pvol *= g->ncell[a] + 2 * gw;
         const int64_t nb = g->ncell[a] / std::max<int32_t>(1, g->box[a]);
         nboxes *= nb;
@@ -566,8 +566,8 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     *out = nullptr;
     const pic_grid_desc& g = *desc;
     if (g.dim != 2 && g.dim != 3) return fail(nullptr, PIC_EINVAL, "dim must be 2 or 3");
-    if (g.shape_order != 1 && g.shape_order != 2)
-        return fail(nullptr, PIC_EINVAL, "shape_order must be 1 or 2");
+    if (g.shape_order < 1 || g.shape_order > 3)
+        return fail(nullptr, PIC_EINVAL, "shape_order must be 1, 2 or 3");
     if (g.dim == 2 && (g.ncell[1] != 1 || g.box[1] != 1))
         return fail(nullptr, PIC_EINVAL, "2D runs need ncell[1] == box[1] == 1");
     for (int a = 0; a < 3; ++a) {
@@ -609,7 +609,8 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     for (int a = 0; a < 3; ++a) {
         bool act = !(g.dim == 2 && a == 1);
         h.n[a] = (int)g.ncell[a];
-        h.g[a] = act ? (a == 0 ? PIC_GX : PIC_G) : 0;
+        // x guard: even tile origin - E/B halo + guard must be even (TMA)
+        h.g[a] = act ? (a == 0 ? (g.shape_order == 3 ? PIC_GX + 1 : PIC_GX) : PIC_G) : 0;
         h.pn[a] = h.n[a] + 2 * h.g[a];
         h.bsz[a] = g.box[a];
         h.nb[a] = h.n[a] / h.bsz[a];
@@ -633,7 +634,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     for (int a = 0; a < 3; ++a) {
         bool act = !(g.dim == 2 && a == 1);
         h.dtd[a] = act ? h.dt / h.d[a] : 0.0;
-        h.ebs[a] = act ? h.T[a] + (h.order == 1 ? 2 : 3) : 1;
+        h.ebs[a] = act ? h.T[a] + (h.order == 1 ? 2 : h.order == 2 ? 3 : 4) : 1;
         h.js[a] = act ? h.T[a] + (h.order == 1 ? 3 : 5) : 1;
     }
     if (h.order == 2) h.ebs[0] += 1;

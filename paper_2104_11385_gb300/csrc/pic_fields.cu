@@ -177,7 +177,7 @@ __global__ void rho_kernel(const SimDev* __restrict__ sims, int sp_idx, double* 
          p += (int64_t)gridDim.x * blockDim.x) {
         double X[3] = {sp.cur[0][p], DIM == 3 ? sp.cur[1][p] : 0.0, sp.cur[2][p]};
         int s[3];
-        double w[3][3];
+        double w[3][4];
         for (int a = 0; a < 3; ++a) {
             if (DIM == 2 && a == 1) { s[a] = 0; w[a][0] = 1.0; continue; }
             if (ORDER == 1) {
@@ -185,6 +185,14 @@ __global__ void rho_kernel(const SimDev* __restrict__ sims, int sp_idx, double* 
                 double f = X[a] - s[a];
                 w[a][0] = 1.0 - f;
                 w[a][1] = f;
+            } else if (ORDER == 3) {
+                const int i = (int)floor(X[a]);
+                const double f = X[a] - i, g = 1.0 - f;
+                s[a] = i - 1;
+                w[a][0] = g * g * g / 6.0;
+                w[a][1] = 2.0 / 3.0 - f * f + 0.5 * f * f * f;
+                w[a][2] = 2.0 / 3.0 - g * g + 0.5 * g * g * g;
+                w[a][3] = f * f * f / 6.0;
             } else {
                 int c = (int)floor(X[a] + 0.5);
                 double d = X[a] - c;
@@ -309,9 +317,11 @@ cudaError_t pic_launch_rho(const SimDev* dsim, const SimDev& h, double* rho, dou
         int64_t cap = h.sp[s].cap;
         int nb = blocks_for(cap, 256);
         if (h.dim == 3 && h.order == 1) rho_kernel<3, 1><<<nb, 256, 0, st>>>(dsim, s, rho);
-        else if (h.dim == 3) rho_kernel<3, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else if (h.dim == 3 && h.order == 2) rho_kernel<3, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else if (h.dim == 3) rho_kernel<3, 3><<<nb, 256, 0, st>>>(dsim, s, rho);
         else if (h.order == 1) rho_kernel<2, 1><<<nb, 256, 0, st>>>(dsim, s, rho);
-        else rho_kernel<2, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else if (h.order == 2) rho_kernel<2, 2><<<nb, 256, 0, st>>>(dsim, s, rho);
+        else rho_kernel<2, 3><<<nb, 256, 0, st>>>(dsim, s, rho);
     }
     return cudaGetLastError();
 }

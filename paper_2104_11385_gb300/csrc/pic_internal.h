@@ -22,9 +22,9 @@
 #include "../../include/pic_api.h"
 
 #define PIC_G 2        // guard cells per side in y and z of the padded field arrays
-#define PIC_GX 3       // guard cells per side in x: odd, so that a tile's TMA box, which
-                       // starts one cell below an even tile origin, starts at an even
-                       // padded x (x * 8 bytes must be a multiple of 16)
+#define PIC_GX 3       // guard cells per side in x (4 for cubic shapes): a tile's TMA box
+                       // starts 1 cell (2 for cubic) below an even tile origin and must
+                       // start at an even padded x (x * 8 bytes a multiple of 16)
 #define PIC_MAXSP 4    // species per simulation
 #define PIC_NCOMP 9
 

@@ -131,17 +131,28 @@ struct Support {
     double w[ORDER + 1];
 };
 
+// cubic B-spline weights of the four nodes floor(xi)-1 .. floor(xi)+2, f = frac(xi)
+__device__ __forceinline__ void cubic_weights(double f, double* w) {
+    constexpr double k6 = 1.0 / 6.0, k23 = 2.0 / 3.0;
+    const double g = 1.0 - f;
+    const double f2 = f * f, g2 = g * g;
+    w[0] = (g2 * g) * k6;
+    w[1] = fma(0.5 * f, f2, k23 - f2);
+    w[2] = fma(0.5 * g, g2, k23 - g2);
+    w[3] = (f2 * f) * k6;
+}
+
 // support of a node-centred quantity at xi (cells, from the tile origin)
 template <int ORDER>
 __device__ __forceinline__ Support<ORDER> support(double xi) {
     Support<ORDER> r;
     double f;
     const int i = ifloor_frac(xi, f);
-    if (ORDER == 1) {
+    if constexpr (ORDER == 1) {
         r.s = i;
         r.w[0] = 1.0 - f;
         r.w[1] = f;
-    } else {
+    } else if constexpr (ORDER == 2) {
         // nearest node c = floor(xi + 1/2), d = xi - c in [-1/2, 1/2)
         const bool up = ge_half(f);
         const double d = up ? f - 1.0 : f;
@@ -149,7 +160,10 @@ __device__ __forceinline__ Support<ORDER> support(double xi) {
         r.s = i + (up ? 1 : 0) - 1;
         r.w[0] = 0.5 * (a * a);
         r.w[1] = fma(-d, d, 0.75);
-        r.w[ORDER] = 0.5 * (b * b);
+        r.w[2] = 0.5 * (b * b);
+    } else {
+        r.s = i - 1;
+        cubic_weights(f, r.w);
     }
     return r;
 }
@@ -161,7 +175,7 @@ __device__ __forceinline__ void supports(double xi, Support<ORDER>& nd, Support<
     double f;
     const int i = ifloor_frac(xi, f);
     const bool up = ge_half(f);
-    if (ORDER == 1) {
+    if constexpr (ORDER == 1) {
         nd.s = i;
         nd.w[0] = 1.0 - f;
         nd.w[1] = f;
@@ -169,29 +183,42 @@ __device__ __forceinline__ void supports(double xi, Support<ORDER>& nd, Support<
         hf.s = up ? i : i - 1;
         hf.w[0] = 1.0 - g;
         hf.w[1] = g;
-    } else {
+    } else if constexpr (ORDER == 2) {
         const double d = up ? f - 1.0 : f;  // node: xi - floor(xi + 1/2)
         const double a = 0.5 - d, b = 0.5 + d;
         nd.s = i + (up ? 1 : 0) - 1;
         nd.w[0] = 0.5 * (a * a);
         nd.w[1] = fma(-d, d, 0.75);
-        nd.w[ORDER] = 0.5 * (b * b);
+        nd.w[2] = 0.5 * (b * b);
         const double h = f - 0.5;  // half: (xi - 1/2) - floor(xi), nearest half-node floor(xi)
         const double ah = 0.5 - h, bh = 0.5 + h;
         hf.s = i - 1;
         hf.w[0] = 0.5 * (ah * ah);
         hf.w[1] = fma(-h, h, 0.75);
-        hf.w[ORDER] = 0.5 * (bh * bh);
+        hf.w[2] = 0.5 * (bh * bh);
+    } else {
+        nd.s = i - 1;
+        cubic_weights(f, nd.w);
+        const double g = f + (up ? -0.5 : 0.5);
+        hf.s = (up ? i : i - 1) - 1;
+        cubic_weights(g, hf.w);
     }
 }
 
 // interpolation of one component from a shared tile with extents (SX, SY)
+// E/B tile halo below the tile origin: 1 cell (orders 1, 2), 2 cells (order 3)
+template <int ORDER>
+struct EBHalo {
+    static constexpr int lo = ORDER == 3 ? 2 : 1;
+};
+
 template <int ORDER, int DIM>
 __device__ __forceinline__ double interp(const double* __restrict__ F, int SX, int SY,
                                          const Support<ORDER>& sx, const Support<ORDER>& sy,
                                          const Support<ORDER>& sz) {
-    // tile column 0 is local cell -1
-    if (ORDER == 1) {
+    // tile column 0 is local cell -EBHalo<ORDER>::lo
+    constexpr int H = EBHalo<ORDER>::lo;
+    if constexpr (ORDER == 1) {
         // linear: nested lerps a + f (b - a) need only the fractional parts
         auto lerp = [](double a, double b, double f) { return fma(f, b - a, a); };
         const double fx = sx.w[1];
@@ -208,14 +235,14 @@ __device__ __forceinline__ double interp(const double* __restrict__ F, int SX, i
             const double* r1 = r0 + SX;
             return lerp(lerp(r0[0], r0[1], fx), lerp(r1[0], r1[1], fx), sz.w[1]);
         }
-    } else if (DIM == 3) {
+    } else if constexpr (DIM == 3) {
         double acc = 0.0;
 #pragma unroll
         for (int c = 0; c <= ORDER; ++c) {
             double pl = 0.0;
 #pragma unroll
             for (int b = 0; b <= ORDER; ++b) {
-                const double* row = F + ((sz.s + 1 + c) * SY + (sy.s + 1 + b)) * SX + (sx.s + 1);
+                const double* row = F + ((sz.s + H + c) * SY + (sy.s + H + b)) * SX + (sx.s + H);
                 double r = sx.w[0] * row[0];
 #pragma unroll
                 for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
@@ -228,7 +255,7 @@ __device__ __forceinline__ double interp(const double* __restrict__ F, int SX, i
         double acc = 0.0;
 #pragma unroll
         for (int c = 0; c <= ORDER; ++c) {
-            const double* row = F + (sz.s + 1 + c) * SX + (sx.s + 1);
+            const double* row = F + (sz.s + H + c) * SX + (sx.s + H);
             double r = sx.w[0] * row[0];
 #pragma unroll
             for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
@@ -580,6 +607,9 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         if (ORDER == 1) {
             in = nd[0].s >= 0 && nd[0].s < S.T[0] && nd[2].s >= 0 && nd[2].s < S.T[2];
             if (DIM == 3) in = in && nd[1].s >= 0 && nd[1].s < S.T[1];
+        } else if (ORDER == 3) {  // node support start = floor(xl) - 1
+            in = nd[0].s >= -1 && nd[0].s < S.T[0] - 1 && nd[2].s >= -1 && nd[2].s < S.T[2] - 1;
+            if (DIM == 3) in = in && nd[1].s >= -1 && nd[1].s < S.T[1] - 1;
         } else {
             in = hf[0].s >= -1 && hf[0].s < S.T[0] - 1 && hf[2].s >= -1 && hf[2].s < S.T[2] - 1;
             if (DIM == 3) in = in && hf[1].s >= -1 && hf[1].s < S.T[1] - 1;
@@ -809,9 +839,10 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     if (threadIdx.x == 0) {
                         fence_proxy_async();
                         mbar_expect_tx(&bar, (uint32_t)(6 * P.eb_vol * sizeof(double)));
-                        const int x0 = cur.o[0] - 1 + S.g[0];
-                        const int y0 = (DIM == 3) ? cur.o[1] - 1 + S.g[1] : 0;
-                        const int z0 = cur.o[2] - 1 + S.g[2];
+                        constexpr int H = EBHalo<ORDER>::lo;
+                        const int x0 = cur.o[0] - H + S.g[0];
+                        const int y0 = (DIM == 3) ? cur.o[1] - H + S.g[1] : 0;
+                        const int z0 = cur.o[2] - H + S.g[2];
 #pragma unroll
                         for (int c = 0; c < 6; ++c)
                             tma_load_3d(sEB + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
@@ -1033,7 +1064,7 @@ size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads) 
     int ebs[3], js[3];
     for (int a = 0; a < 3; ++a) {
         bool act = !(dim == 2 && a == 1);
-        ebs[a] = act ? T[a] + (order == 1 ? 2 : 3) : 1;
+        ebs[a] = act ? T[a] + (order == 1 ? 2 : order == 2 ? 3 : 4) : 1;
         js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
     }
     if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
@@ -1056,6 +1087,8 @@ cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_
     if (dim == 3 && order == 2) return launch_particles_t<3, 2>(cfg, smem, sched, sims, st);
     if (dim == 2 && order == 1) return launch_particles_t<2, 1>(cfg, smem, sched, sims, st);
     if (dim == 2 && order == 2) return launch_particles_t<2, 2>(cfg, smem, sched, sims, st);
+    if (dim == 3 && order == 3) return launch_particles_t<3, 3>(cfg, smem, sched, sims, st);
+    if (dim == 2 && order == 3) return launch_particles_t<2, 3>(cfg, smem, sched, sims, st);
     return cudaErrorInvalidValue;
 }
 
@@ -1083,6 +1116,8 @@ int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t sme
     if (dim == 3 && order == 2) return occupancy_t<3, 2>(minb, threads, smem);
     if (dim == 2 && order == 1) return occupancy_t<2, 1>(minb, threads, smem);
     if (dim == 2 && order == 2) return occupancy_t<2, 2>(minb, threads, smem);
+    if (dim == 3 && order == 3) return occupancy_t<3, 3>(minb, threads, smem);
+    if (dim == 2 && order == 3) return occupancy_t<2, 3>(minb, threads, smem);
     return 0;
 }
 
@@ -1091,6 +1126,8 @@ cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
     if (dim == 3 && order == 2) return prepare_t<3, 2>(smem);
     if (dim == 2 && order == 1) return prepare_t<2, 1>(smem);
     if (dim == 2 && order == 2) return prepare_t<2, 2>(smem);
+    if (dim == 3 && order == 3) return prepare_t<3, 3>(smem);
+    if (dim == 2 && order == 3) return prepare_t<2, 3>(smem);
     return cudaErrorInvalidValue;
 }
 

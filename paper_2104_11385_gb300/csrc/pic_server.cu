@@ -288,7 +288,7 @@ const char* pic_server_last_error(const pic_server* s) { return s ? s->err.c_str
 pic_status pic_server_create(const pic_server_desc* d, pic_server** out) {
     if (!d || !out) return pic_record_error(PIC_EINVAL, "null argument");
     *out = nullptr;
-    if ((d->dim != 2 && d->dim != 3) || (d->shape_order != 1 && d->shape_order != 2) ||
+    if ((d->dim != 2 && d->dim != 3) || d->shape_order < 1 || d->shape_order > 3 ||
         d->max_active < 1 || d->max_active > 4096 || d->hbm_budget_bytes <= 0)
         return pic_record_error(PIC_EINVAL, "bad server description");
     pic_server* s = new (std::nothrow) pic_server();

@@ -73,6 +73,8 @@ CASES = [
     (3, (16, 24, 32), (16, 8, 16), (0.25, 0.3, 0.3), 1),
     (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.35), 1),
     (2, (32, 1, 64), (32, 1, 32), (0.3, 1.0, 0.3), 2),
+    (3, (16, 16, 24), (8, 8, 8), (0.3, 0.3, 0.35), 3),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.3), 3),
 ]
 
 
@@ -96,13 +98,13 @@ def test_uniform32_full_size_parity():
     compare(sim, ref, wl)
 
 
-@pytest.mark.parametrize("dim", [3, 2])
-def test_absorbing_boundary_and_laser_parity(dim):
+@pytest.mark.parametrize("dim,order", [(3, 1), (2, 1), (2, 3)])
+def test_absorbing_boundary_and_laser_parity(dim, order):
     if dim == 3:
         n, box, dx = (16, 16, 48), (8, 8, 16), (0.3, 0.3, 0.3)
     else:
         n, box, dx = (32, 1, 64), (16, 1, 16), (0.3, 1.0, 0.3)
-    wl = workloads.random_plasma(300 + dim, dim, n, box, dx, 1, nspecies=2, npart=3000, umax=3.0,
+    wl = workloads.random_plasma(300 + dim, dim, n, box, dx, order, nspecies=2, npart=3000, umax=3.0,
                                  absorb=6, laser=True)
     sim, ref = make_gpu(wl), make_oracle(wl)
     sim.step(12)

@@ -35,7 +35,8 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic FP64 flops per particle update, in-cell path (3D linear: gather 126,
 # local positions and half-node shifts 6, Boris push 70, Esirkepov deposit 73, positions 3)
-FLOPS_PER_PARTICLE = {(3, 1): 278.0, (3, 2): 766.0, (2, 1): 170.0, (2, 2): 350.0}
+FLOPS_PER_PARTICLE = {(3, 1): 278.0, (3, 2): 766.0, (3, 3): 1594.0, (2, 1): 170.0, (2, 2): 350.0,
+                      (2, 3): 548.0}
 BYTES_PER_PARTICLE = 104.0  # read x,y,z,ux,uy,uz,w (56) + write x..uz (48)
 BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 
@@ -46,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="foil256", choices=["foil256", "uniform32", "lognormal4096"])
+    ap.add_argument("--workload", default="foil256",
+                    choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d"])
     ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (debug only)")
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
@@ -87,6 +89,8 @@ def make_workload(name, scale, seed_offset=0):
         return W.foil256(seed=2 + seed_offset, scale=scale)
     if name == "uniform32":
         return W.uniform32(seed=1 + seed_offset)
+    if name == "laser_ion_2d":
+        return W.laser_ion_2d(seed=6 + seed_offset, scale=scale)
     return W.lognormal(seed=3 + seed_offset)
 
 
@@ -299,7 +303,7 @@ def run_ours(args, rank, world):
         "gpu_launches": int(round(kernels_per_step * args.steps)),
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "pic_particle_kernel<3,1> (gather+Boris+Esirkepov+cost)",
+                     "kernel": "pic_particle_kernel<%d,%d> (gather+Boris+Esirkepov+cost)" % (wl["dim"], wl["order"]),
                      "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.19 TFLOP/s)",
                      "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                              "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE}},

@@ -23,6 +23,17 @@ particle counts):
                  a mean density n0 = 1, quadratic shape, periodic.
   foil_scale     3D laser-foil at scale: 512 x 512 x 1024 cells in 32^3 boxes,
                  foil 16 cells thick at 64 ppc per species.
+  laser_ion_2d   the paper's 2D3V laser-ion setup (Sec. 3.1) at one-GPU scale:
+                 (z, x) domain 30 um x 30 um (z in [-10, 20] um, x in [-15, 15]
+                 um) in 1920^2 cells (dx = 0.0195 lambda0) and 64^2-cell boxes;
+                 hydrogen disk of radius 5 um + 2 um slope (exponential, 50 nm
+                 scale length, constant macro-particle number) at 5 n_c;
+                 electrons with 0.01 m_e c Gaussian momenta in x and z, protons
+                 at rest; laser a0 = 25, lambda0 = 0.8 um, x-polarised, waist
+                 4 um, 10 fs amplitude e-folding time, from z = -9 um; cubic
+                 shapes; 32 macro-particles per cell per species (the paper:
+                 900, which does not fit one GPU); scale = 2 gives the paper's
+                 960^2 run.
 The ``scale`` argument shrinks a workload for the oracle-sized parity cases
 (same recipe, fewer cells / particles).
 """
@@ -169,3 +180,45 @@ def random_fields(seed, ncell, amp=0.05):
     r = _rng(seed)
     n = ncell[0] * ncell[1] * ncell[2]
     return [amp * r.normal(size=n) for _ in range(6)]
+
+
+def laser_ion_2d(seed=6, ppc=32, scale=1, absorb=32):
+    """The paper's 2D3V laser-ion acceleration setup at one-GPU scale."""
+    r = _rng(seed)
+    um = 2.0 * math.pi / 0.8  # one micrometre in c/omega0 for lambda0 = 0.8 um
+    n = 1920 // scale
+    L = 30.0 * um
+    dx = L / n
+    xc, zc = 15.0 * um, 10.0 * um  # the disk centre (x = z = 0) in domain coordinates
+    rcore, rslope, lscale = 5.0 * um, 7.0 * um, 0.05 * um
+    ii = np.arange(n)
+    cx = (ii + 0.5) * dx - xc
+    cz = (ii + 0.5) * dx - zc
+    CZ, CX = np.meshgrid(cz, cx, indexing="ij")
+    inside = np.sqrt(CX * CX + CZ * CZ) < rslope
+    kz, kx = np.nonzero(inside)
+    ncell = kz.size
+    npart = ncell * ppc
+    cell_x = np.repeat(kx, ppc)
+    cell_z = np.repeat(kz, ppc)
+    x = (cell_x + r.uniform(0.0, 1.0, npart)) * dx
+    z = (cell_z + r.uniform(0.0, 1.0, npart)) * dx
+    rad = np.sqrt((x - xc) ** 2 + (z - zc) ** 2)
+    dens = 5.0 * np.where(rad <= rcore, 1.0, np.exp(-(rad - rcore) / lscale))
+    w = dens * dx * dx / ppc
+    ux = r.normal(0.0, 0.01, npart)
+    uz = r.normal(0.0, 0.01, npart)
+    zeros = np.zeros(npart)
+    e = _species(-1.0, 1.0, x, zeros, z, ux, zeros.copy(), uz, w, id0=0)
+    p = _species(1.0, PROTON_MASS, x.copy(), zeros.copy(), z.copy(), zeros.copy(), zeros.copy(),
+                 zeros.copy(), w.copy(), id0=npart)
+    fs = 2.0 * math.pi * 0.299792458 / 0.8  # one femtosecond in 1/omega0
+    tau = 10.0 * fs
+    laser = {"a0": 25.0, "w0": 4.0 * um, "tau": tau, "t_peak": 2.5 * tau, "omega": 1.0,
+             "xc": xc, "yc": 0.0, "k_ant": int(round(1.0 * um / dx))}
+    dt = 0.999 * dx / math.sqrt(2.0)
+    return {
+        "name": f"laser_ion_2d_{n}", "dim": 2, "ncell": (n, 1, n), "box": (64 // scale, 1, 64 // scale),
+        "dx": (dx, 1.0, dx), "dt": dt, "order": 3, "absorb": absorb, "species": [e, p],
+        "laser": laser, "rho0": 0.0, "steps": int(round(150.0 * fs / dt)), "lb_interval": 10,
+    }

@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=1, choices=[1, 2],
+                    help="particle push arithmetic of the main arm: 1 FP64, 2 float-float")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
@@ -192,6 +195,7 @@ def run_ours(args, rank, world):
     sim.step(1)                                      # measure per-box clock costs once
     sim.rebalance(**dict(lbkw, theta=0.0))           # initial cost-driven mapping
     sim.set_lb_params(**lbkw)
+    sim.set_launch(precision=args.precision)
     if args.threads or args.ctas_per_sm:
         sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
         tuned = sim.get_launch()
@@ -226,6 +230,30 @@ def run_ours(args, rank, world):
     del sim
     torch.cuda.empty_cache()
 
+    # ---- the mixed-precision variant (float-float push, FP64 storage and sums)
+    mixed = None
+    if not args.no_mixed and args.precision == 1:
+        sim = pic.from_workload(wl, stream=stream.cuda_stream)
+        sim.set_launch(precision=2)
+        sim.step(1)
+        sim.rebalance(**dict(lbkw, theta=0.0))
+        sim.set_lb_params(**lbkw)
+        mtuned = sim.autotune(steps_per_candidate=2)
+        sim.step(args.warmup)
+        ms_mixed = timed(sim, args.steps)
+        sim.set_profiling(True)
+        sim.step(min(args.steps, 10))
+        mst = sim.stats()
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        mixed = {"value": nparts * args.steps * world / (ms_mixed / 1e3), "unit": "particle-updates/s",
+                 "ms_per_step": ms_mixed / args.steps,
+                 "particle_kernel_ms": mst["ms_particle"] / max(mst["steps"], 1), "launch": mtuned,
+                 "arithmetic": "float-float (FP32 pairs, ~48-bit significand) gather, Boris and deposit "
+                               "weights; FP64 storage, positions and current sums; parity 1e-10 vs the "
+                               "FP64 oracle (tests/test_gpu_parity.py)"}
+
     # ---- the paper's cost strategies side by side (same schedule, same tuning)
     cost_arms = {"device_clock": nparts * args.steps * world / (ms_bal / 1e3)}
     if not args.no_cost_arms:
@@ -235,7 +263,7 @@ def run_ours(args, rank, world):
             sim.step(1)
             sim.rebalance(**dict(ckw, theta=0.0))
             sim.set_lb_params(**ckw)
-            sim.set_launch(**{k: tuned[k] for k in ("threads", "ctas_per_sm", "split")})
+            sim.set_launch(**{k: tuned[k] for k in ("threads", "ctas_per_sm", "split")}, precision=args.precision)
             sim.step(args.warmup)
             cost_arms[name] = nparts * args.steps * world / (timed(sim, args.steps) / 1e3)
             sim.close()
@@ -313,6 +341,7 @@ def run_ours(args, rank, world):
         "other_schedule": {"sched": other, "value": nparts * args.steps * world / (ms_other / 1e3),
                            "ms_per_step": ms_other / args.steps},
         "cost_strategies": cost_arms,
+        "mixed_precision": mixed,
         "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
         "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
                               "sort": st["ms_sort"] / max(st["steps"], 1)},
@@ -520,11 +549,12 @@ def main():
         line = {"metric": "particle-updates/s", "value": res["value"], "unit": "particle-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded PCG64 workload recipe)",
-                "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
+                "vs_baseline": None, "dtype": "f64" if args.precision == 1 else "float-float",
+                "data": "synthetic (seeded PCG64 workload recipe)", "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
                 "static_order": res["static_order"], "other_schedule": res["other_schedule"],
-                "cost_strategies": res["cost_strategies"], "batched_uneven_boxes": c3,
+                "cost_strategies": res["cost_strategies"], "mixed_precision": res["mixed_precision"],
+                "batched_uneven_boxes": c3,
                 "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
                 "phase_ms_per_step": res["phase_ms_per_step"], "lb": res["lb"], "server": server}

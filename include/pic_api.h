@@ -265,11 +265,18 @@ pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const d
 
 /* Launch configuration of the persistent particle kernel and the work
  * splitting (the autotuner's knobs).  Any field <= 0 keeps its value.
- *   threads       threads per CTA (128, 256, 512).
- *   ctas_per_sm   persistent CTAs per SM (1 or 2; capped by shared memory).
- *   split         target work units per worker when boxes are cut. */
+ *   threads       threads per CTA (a multiple of 32, at most 256).
+ *   ctas_per_sm   persistent CTAs per SM (1 or 2; 2 selects the kernel
+ *                 variant compiled for 128 registers; capped by occupancy).
+ *   split         target work units per worker when boxes are cut.
+ *   precision     arithmetic of the particle push: 1 FP64 (default);
+ *                 2 float-float (pairs of FP32 with error-free
+ *                 transformations, ~48-bit significand) for gather, Boris and
+ *                 deposit weights, with FP64 storage, positions, index math and
+ *                 current accumulation -- the mixed-precision variant; 0 keeps
+ *                 the current setting.  The autotuner never changes it. */
 typedef struct {
-    int threads, ctas_per_sm, split;
+    int threads, ctas_per_sm, split, precision;
 } pic_launch_cfg;
 pic_status pic_set_launch(pic_sim* sim, const pic_launch_cfg* cfg);
 pic_status pic_get_launch(const pic_sim* sim, pic_launch_cfg* cfg);

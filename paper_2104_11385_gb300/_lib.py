@@ -53,7 +53,10 @@ class LBResult(ctypes.Structure):
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("threads", _int), ("ctas_per_sm", _int), ("split", _int)]
+    _fields_ = [("threads", _int), ("ctas_per_sm", _int), ("split", _int), ("precision", _int)]
+
+
+PREC_FP64, PREC_FLOAT_FLOAT = 1, 2
 
 
 class Stats(ctypes.Structure):

@@ -81,6 +81,7 @@ struct pic_sim {
     int split = 16;
     int ctas = 0;
     int minb = 1;
+    int prec = 0;  // 0 FP64, 1 float-float particle push
     size_t smem = 0;
     // load balancing
     pic_lb_params lb{};
@@ -422,7 +423,7 @@ pic_status enqueue_step(pic_sim* s, bool with_events) {
     if (with_events) CU(s, cudaEventRecord(s->ev[0], s->stream));
     CU(s, cudaMemsetAsync(h.F[6], 0, jbytes, s->stream));
     if (h.nsp > 0) {
-        LaunchCfg cfg{s->threads, s->ctas, s->minb};
+        LaunchCfg cfg{s->threads, s->ctas, s->minb, s->prec};
         CU(s, pic_launch_particles(h.dim, h.order, cfg, s->smem, s->ds, s->d, s->stream));
     }
     if (with_events) CU(s, cudaEventRecord(s->ev[1], s->stream));
@@ -468,7 +469,7 @@ pic_status configure_launch(pic_sim* s) {
     // persistent grid: every CTA resident (registers, shared memory, threads)
     // ctas_per_sm >= 2 selects the kernel variant compiled for 2 resident CTAs
     s->minb = s->ctas_per_sm >= 2 ? 2 : 1;
-    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->minb, s->threads, s->smem);
+    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->minb, s->threads, s->smem, s->prec);
     if (resident < 1) return fail(s, PIC_EUNSUPPORTED, "particle kernel does not fit on an SM");
     int per_sm = std::max(1, std::min(s->ctas_per_sm, resident));
     s->ctas = s->nsm * per_sm;
@@ -1057,6 +1058,11 @@ pic_status pic_set_launch(pic_sim* s, const pic_launch_cfg* cfg) {
     }
     const int old_split = s->split;
     if (cfg->split > 0) s->split = cfg->split;
+    if (cfg->precision < 0 || cfg->precision > 2) return fail(s, PIC_EINVAL, "precision must be 0, 1 or 2");
+    if (cfg->precision > 0) {
+        s->prec = cfg->precision - 1;
+        s->graph_dirty = true;
+    }
     const int old = s->ctas;
     TRY(configure_launch(s));
     if (s->ctas != old || s->split != old_split) TRY(replan(s));
@@ -1068,6 +1074,7 @@ pic_status pic_get_launch(const pic_sim* s, pic_launch_cfg* cfg) {
     cfg->threads = s->threads;
     cfg->ctas_per_sm = s->ctas / std::max(1, s->nsm);
     cfg->split = s->split;
+    cfg->precision = s->prec + 1;
     return PIC_OK;
 }
 
@@ -1081,7 +1088,7 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     const int cps_c[2] = {1, 2};
     const int split_c[3] = {4, 16, 64};
     float best_ms = 1e30f;
-    pic_launch_cfg best_cfg{s->threads, s->ctas_per_sm, s->split};
+    pic_launch_cfg best_cfg{s->threads, s->ctas_per_sm, s->split, 0};
     cudaEvent_t a, b;
     CU(s, cudaEventCreate(&a));
     CU(s, cudaEventCreate(&b));
@@ -1092,7 +1099,7 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
         for (int c : cps_c)
             for (int sp : split_c) {
                 if (!splits && sp != split_c[1]) continue;  // no cut boxes without balancing
-                pic_launch_cfg cfg{t, c, sp};
+                pic_launch_cfg cfg{t, c, sp, 0};
                 TRY(pic_set_launch(s, &cfg));
                 if (s->ctas / s->nsm != c) continue;  // not resident: skip
                 TRY(pic_step(s, 1));
@@ -1104,7 +1111,7 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
                 cudaEventElapsedTime(&ms, a, b);
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best_cfg = pic_launch_cfg{t, c, sp};
+                    best_cfg = pic_launch_cfg{t, c, sp, 0};
                 }
             }
     s->profiling = prof;

@@ -105,10 +105,21 @@ struct LaunchCfg {
     int threads;
     int ctas;
     int minb;  // register budget variant of the particle kernel: 1 or 2 CTAs per SM
+    int prec;  // arithmetic of the particle push: 0 FP64, 1 float-float
 };
 size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads);
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem);  // outside graph capture
-int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem);  // resident CTAs per SM
+int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem,
+                           int prec);  // resident CTAs per SM
+// per-precision instantiations (pic_particles_f64.cu, pic_particles_dd.cu)
+cudaError_t pic_launch_particles_p0(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
+cudaError_t pic_launch_particles_p1(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
+cudaError_t pic_prepare_particles_p0(int dim, int order, size_t smem);
+cudaError_t pic_prepare_particles_p1(int dim, int order, size_t smem);
+int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t smem);
+int pic_particle_occupancy_p1(int dim, int order, int minb, int threads, size_t smem);
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
                                  const SchedDev* sched, SimDev* sims, cudaStream_t st);
 cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& hsim, cudaStream_t st);

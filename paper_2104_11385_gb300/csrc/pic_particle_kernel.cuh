@@ -1,0 +1,995 @@
+// pic_particle_kernel.cuh -- the particle side of the PIC cycle on sm_103a,
+// templated on the arithmetic of the particle push (included by one
+// translation unit per precision: pic_particles_f64.cu, pic_particles_dd.cu).
+//
+// pic_particle_kernel: persistent CTAs pull work units (a chunk of one box's
+// particles) from cost-ordered lists.  For every tile (sub-box) a unit touches,
+// the guard-extended E/B tile is staged into shared memory by TMA
+// (cp.async.bulk.tensor, local HBM only, no multicast), the current is
+// deposited into a shared-memory J tile with shared FP64 atomics and flushed
+// once per tile into the global J arrays.  Each thread brackets its particle
+// loop with clock64(); the deltas are warp-reduced, summed in shared memory and
+// added once per unit to the box's cost -- the device-clock cost of
+// arXiv 2104.11385 Sec. 2.2 (Fig. 2a); thread 0 adds the unit's %globaltimer
+// span to the box's kernel-time cost.  The same pass writes each particle's new
+// tile key and the per-tile histogram for the re-sort.
+//
+// Physics per particle (the schemes the paper leaves open, Sec. 2.1): field
+// gather with B-spline shapes at each component's Yee location, relativistic
+// Boris push, Esirkepov charge-conserving deposit (Esirkepov 2001).
+#pragma once
+#include <type_traits>
+
+#include "pic_dd.cuh"
+#include "pic_internal.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of %globaltimer.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 0u) {
+            uint64_t now = globaltimer();
+            if (it == 0) t0 = now;
+            else if (now - t0 > 2000000000ull) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Exact floor and fractional part of x.  On GB300 every FP64 instruction,
+// conversions included, issues at the FP64 rate (about 2 per SM per clock), so
+// for 0 <= x < 2^31 both come from integer work on the IEEE-754 bits; other x
+// go through floor().  Both routes give the identical (exact) results.
+__device__ __forceinline__ int ifloor_frac(double x, double& f) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((unsigned long long)b >> 52) - 1023;  // sign set -> e > 1023
+    if (e < 0) {
+        if (b >= 0) {  // 0 <= x < 1
+            f = x;
+            return 0;
+        }
+    } else if (e < 31) {
+        const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        const int sh = 52 - e;
+        const int i = (int)(m >> sh);
+        const unsigned long long fm = m & ((1ull << sh) - 1ull);
+        if (fm == 0ull) {
+            f = 0.0;
+        } else {
+            const int top = 63 - __clzll((long long)fm);
+            const unsigned long long bits = ((unsigned long long)(top - sh + 1023) << 52) |
+                                            ((fm << (52 - top)) & 0xFFFFFFFFFFFFFull);
+            f = __longlong_as_double((long long)bits);
+        }
+        return i;
+    }
+    const double fl = floor(x);
+    f = x - fl;
+    return (int)fl;
+}
+
+// floor of x >= 0 (x < 2^31) by integer work; floor() otherwise
+__device__ __forceinline__ int ifloor(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((unsigned long long)b >> 52) - 1023;
+    if (e < 0 && b >= 0) return 0;
+    if (e >= 0 && e < 31)
+        return (int)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) >> (52 - e));
+    return (int)floor(x);
+}
+
+// x < 0 and x >= y for y > 0 by integer comparison of the bit patterns
+__device__ __forceinline__ bool is_neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool ge_pos(double x, double y) {
+    return __double_as_longlong(x) >= __double_as_longlong(y);
+}
+__device__ __forceinline__ bool ge_half(double f) {  // f >= 0.5 for f >= 0
+    return __double_as_longlong(f) >= 0x3FE0000000000000ll;
+}
+
+// one-dimensional B-spline support: first node and ORDER+1 weights in the
+// arithmetic type R (double, or dd for the float-float variant)
+template <int ORDER, class R>
+struct Support {
+    int s;
+    R w[ORDER + 1];
+};
+
+// cubic B-spline weights of the four nodes floor(xi)-1 .. floor(xi)+2, f = frac(xi)
+template <class R>
+__device__ __forceinline__ void cubic_weights(R f, R* w) {
+    using A = Arith<R>;
+    const R k6 = A::c(1.0 / 6.0), k23 = A::c(2.0 / 3.0), half = A::c(0.5);
+    const R g = A::c(1.0) - f;
+    const R f2 = f * f, g2 = g * g;
+    w[0] = (g2 * g) * k6;
+    w[1] = fma(half * f, f2, k23 - f2);
+    w[2] = fma(half * g, g2, k23 - g2);
+    w[3] = (f2 * f) * k6;
+}
+
+// support of a node-centred quantity at xi (cells, from the tile origin)
+template <int ORDER, class R>
+__device__ __forceinline__ Support<ORDER, R> support(double xi) {
+    using A = Arith<R>;
+    Support<ORDER, R> r;
+    double f;
+    const int i = ifloor_frac(xi, f);
+    if constexpr (ORDER == 1) {
+        r.s = i;
+        const R fr = A::from(f);
+        r.w[0] = A::c(1.0) - fr;
+        r.w[1] = fr;
+    } else if constexpr (ORDER == 2) {
+        // nearest node c = floor(xi + 1/2), d = xi - c in [-1/2, 1/2)
+        const bool up = ge_half(f);
+        const R d = A::from(up ? f - 1.0 : f);
+        const R a = A::c(0.5) - d, b = A::c(0.5) + d;
+        r.s = i + (up ? 1 : 0) - 1;
+        r.w[0] = A::c(0.5) * (a * a);
+        r.w[1] = fma(-d, d, A::c(0.75));
+        r.w[2] = A::c(0.5) * (b * b);
+    } else {
+        r.s = i - 1;
+        cubic_weights<R>(A::from(f), r.w);
+    }
+    return r;
+}
+
+// node and half-node supports of one position (the half-node grid is shifted
+// by +1/2 cell: Ex along x, etc.)
+template <int ORDER, class R>
+__device__ __forceinline__ void supports(double xi, Support<ORDER, R>& nd, Support<ORDER, R>& hf) {
+    using A = Arith<R>;
+    double f;
+    const int i = ifloor_frac(xi, f);
+    const bool up = ge_half(f);
+    const R fr = A::from(f);
+    if constexpr (ORDER == 1) {
+        nd.s = i;
+        nd.w[0] = A::c(1.0) - fr;
+        nd.w[1] = fr;
+        const R g = fr + (up ? A::c(-0.5) : A::c(0.5));  // xi - 1/2 - floor(xi - 1/2)
+        hf.s = up ? i : i - 1;
+        hf.w[0] = A::c(1.0) - g;
+        hf.w[1] = g;
+    } else if constexpr (ORDER == 2) {
+        const R d = up ? fr - A::c(1.0) : fr;  // node: xi - floor(xi + 1/2)
+        const R a = A::c(0.5) - d, b = A::c(0.5) + d;
+        nd.s = i + (up ? 1 : 0) - 1;
+        nd.w[0] = A::c(0.5) * (a * a);
+        nd.w[1] = fma(-d, d, A::c(0.75));
+        nd.w[2] = A::c(0.5) * (b * b);
+        const R h = fr - A::c(0.5);  // half: (xi - 1/2) - floor(xi), nearest half-node floor(xi)
+        const R ah = A::c(0.5) - h, bh = A::c(0.5) + h;
+        hf.s = i - 1;
+        hf.w[0] = A::c(0.5) * (ah * ah);
+        hf.w[1] = fma(-h, h, A::c(0.75));
+        hf.w[2] = A::c(0.5) * (bh * bh);
+    } else {
+        nd.s = i - 1;
+        cubic_weights<R>(fr, nd.w);
+        const R g = fr + (up ? A::c(-0.5) : A::c(0.5));
+        hf.s = (up ? i : i - 1) - 1;
+        cubic_weights<R>(g, hf.w);
+    }
+}
+
+// E/B tile halo below the tile origin: 1 cell (orders 1, 2), 2 cells (order 3)
+template <int ORDER>
+struct EBHalo {
+    static constexpr int lo = ORDER == 3 ? 2 : 1;
+};
+
+// interpolation of one component from a shared tile with extents (SX, SY);
+// the tile holds R values (doubles, or float pairs converted in place)
+template <class R, int ORDER, int DIM>
+__device__ __forceinline__ R interp(const R* __restrict__ F, int SX, int SY, const Support<ORDER, R>& sx,
+                                    const Support<ORDER, R>& sy, const Support<ORDER, R>& sz) {
+    // tile column 0 is local cell -EBHalo<ORDER>::lo
+    constexpr int H = EBHalo<ORDER>::lo;
+    if constexpr (ORDER == 1) {
+        // linear: nested lerps a + f (b - a) need only the fractional parts
+        auto lerp = [](R a, R b, R f) { return fma(f, b - a, a); };
+        const R fx = sx.w[1];
+        if constexpr (DIM == 3) {
+            const R* r00 = F + ((sz.s + H) * SY + (sy.s + H)) * SX + (sx.s + H);
+            const R* r10 = r00 + SX;
+            const R* r01 = r00 + SX * SY;
+            const R* r11 = r01 + SX;
+            const R a0 = lerp(lerp(r00[0], r00[1], fx), lerp(r10[0], r10[1], fx), sy.w[1]);
+            const R a1 = lerp(lerp(r01[0], r01[1], fx), lerp(r11[0], r11[1], fx), sy.w[1]);
+            return lerp(a0, a1, sz.w[1]);
+        } else {
+            const R* r0 = F + (sz.s + H) * SX + (sx.s + H);
+            const R* r1 = r0 + SX;
+            return lerp(lerp(r0[0], r0[1], fx), lerp(r1[0], r1[1], fx), sz.w[1]);
+        }
+    } else if constexpr (DIM == 3) {
+        R acc;
+#pragma unroll
+        for (int c = 0; c <= ORDER; ++c) {
+            R pl;
+#pragma unroll
+            for (int b = 0; b <= ORDER; ++b) {
+                const R* row = F + ((sz.s + H + c) * SY + (sy.s + H + b)) * SX + (sx.s + H);
+                R r = sx.w[0] * row[0];
+#pragma unroll
+                for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
+                pl = (b == 0) ? sy.w[0] * r : fma(sy.w[b], r, pl);
+            }
+            acc = (c == 0) ? sz.w[0] * pl : fma(sz.w[c], pl, acc);
+        }
+        return acc;
+    } else {
+        R acc;
+#pragma unroll
+        for (int c = 0; c <= ORDER; ++c) {
+            const R* row = F + (sz.s + H + c) * SX + (sx.s + H);
+            R r = sx.w[0] * row[0];
+#pragma unroll
+            for (int a = 1; a <= ORDER; ++a) r = fma(sx.w[a], row[a], r);
+            acc = (c == 0) ? sz.w[0] * r : fma(sz.w[c], r, acc);
+        }
+        return acc;
+    }
+}
+
+// Esirkepov node shapes on a common window of W nodes starting at the lower of
+// the two supports: W = ORDER + 1 when the particle keeps its support (the
+// in-cell case, most particles), W = ORDER + 2 when it moves to a neighbour.
+template <int ORDER, int W, class R>
+struct Window {
+    int base;
+    R S0[W];
+    R DS[W];
+};
+
+template <int ORDER, int W, class R>
+__device__ __forceinline__ bool make_window(const Support<ORDER, R>& a, const Support<ORDER, R>& b,
+                                            Window<ORDER, W, R>& win) {
+    int base = min(a.s, b.s);
+    int oa = a.s - base, ob = b.s - base;
+    if (oa > W - ORDER - 1 || ob > W - ORDER - 1) return false;
+    win.base = base;
+    const R zero = Arith<R>::c(0.0);
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        R s0 = zero, s1 = zero;
+#pragma unroll
+        for (int k = 0; k <= ORDER; ++k) {
+            s0 = (l - oa == k) ? a.w[k] : s0;
+            s1 = (l - ob == k) ? b.w[k] : s1;
+        }
+        win.S0[l] = s0;
+        win.DS[l] = s1 - s0;
+    }
+    return true;
+}
+
+struct Tile {
+    int sim;
+    int t;
+    int o[3];  // origin cell
+};
+
+__device__ __forceinline__ void tile_origin(const SimDev& S, int t, int o[3]) {
+    int b = t / S.tiles_per_box, lt = t - b * S.tiles_per_box;
+    int bx = b % S.nb[0], by = (b / S.nb[0]) % S.nb[1], bz = b / (S.nb[0] * S.nb[1]);
+    int tx = lt % S.tpb[0], ty = (lt / S.tpb[0]) % S.tpb[1], tz = lt / (S.tpb[0] * S.tpb[1]);
+    o[0] = bx * S.bsz[0] + tx * S.T[0];
+    o[1] = by * S.bsz[1] + ty * S.T[1];
+    o[2] = bz * S.bsz[2] + tz * S.T[2];
+}
+
+__device__ __forceinline__ int modi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+// tile key of a global cell (box-major numbering)
+__device__ __forceinline__ int tile_key(const SimDev& S, int ix, int iy, int iz) {
+    int bx = ix / S.bsz[0], by = iy / S.bsz[1], bz = iz / S.bsz[2];
+    int tx = (ix - bx * S.bsz[0]) / S.T[0];
+    int ty = (iy - by * S.bsz[1]) / S.T[1];
+    int tz = (iz - bz * S.bsz[2]) / S.T[2];
+    int b = (bz * S.nb[1] + by) * S.nb[0] + bx;
+    return b * S.tiles_per_box + (tz * S.tpb[1] + ty) * S.tpb[0] + tx;
+}
+
+__device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
+    unsigned act = __activemask();
+    unsigned peers = __match_any_sync(act, key);
+    int lane = threadIdx.x & 31;
+    if (lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+}
+
+// Shared-memory layout: six E/B tiles (TMA destinations), three J tiles, and
+// per-warp ring buffers of cell-crossing particles (struct of arrays, WQ
+// slots per warp, up to 8 warps).
+constexpr int WQ = 64;
+constexpr int QMAXWARPS = 8;
+// queue fields: 0 xl, 1 zl, 2 dX, 3 dZ, 4 qw, 5 yl (3D) or vy (2D), 6 dY (3D)
+template <int DIM>
+struct QFields {
+    static constexpr int n = DIM == 3 ? 7 : 6;
+};
+
+struct SmemPlan {
+    int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
+    int j_stride;   // doubles per J component
+    int eb_vol, j_vol;
+    size_t bytes;
+};
+
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3]) {
+    SmemPlan p;
+    p.eb_vol = ebs[0] * ebs[1] * ebs[2];
+    p.j_vol = js[0] * js[1] * js[2];
+    p.eb_stride = (p.eb_vol + 15) & ~15;
+    p.j_stride = (p.j_vol + 1) & ~1;
+    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
+    return p;
+}
+
+template <int DIM, int ORDER>
+__device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restrict__ sJ,
+                        const SmemPlan& P) {
+    const int jx = S.js[0], jy = S.js[1];
+    for (int idx = threadIdx.x; idx < 3 * P.j_vol; idx += blockDim.x) {
+        int comp = idx / P.j_vol, r = idx - comp * P.j_vol;
+        double v = sJ[comp * P.j_stride + r];
+        if (v == 0.0) continue;
+        int a = r % jx, b = (r / jx) % jy, c = r / (jx * jy);
+        int gx = modi(tl.o[0] - S.jlo + a, S.n[0]);
+        int gy = (DIM == 3) ? modi(tl.o[1] - S.jlo + b, S.n[1]) : 0;
+        int gz = modi(tl.o[2] - S.jlo + c, S.n[2]);
+        atomicAdd(S.F[6 + comp] + pidx(S, gx, gy, gz), v);
+    }
+}
+
+
+// shared-memory J atomics take doubles; a float-float value is merged first
+template <class R>
+__device__ __forceinline__ void jadd(double* p, R v) {
+    atomicAdd(p, Arith<R>::to(v));
+}
+
+// Esirkepov deposit of one particle into the shared J tile on windows of W
+// nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
+// Prefix sums of DS along each current's own direction times the transverse
+// weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3 = A_a A_b + DS_a DS_b / 12
+// with A = S0 + DS/2.  qw and vy in R; the prefactors -1/(dA dt) come from jf.
+template <class R, int DIM, int ORDER, int W>
+__device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ, const SmemPlan& P,
+                                        R qw, R vy, const R* jf, const Support<ORDER, R>& n0,
+                                        const Support<ORDER, R>& n1, const Support<ORDER, R>& n2,
+                                        const Support<ORDER, R>& m0, const Support<ORDER, R>& m1,
+                                        const Support<ORDER, R>& m2) {
+    using A = Arith<R>;
+    Window<ORDER, W, R> wx, wy, wz;
+    bool ok = make_window<ORDER, W, R>(n0, m0, wx) && make_window<ORDER, W, R>(n2, m2, wz);
+    if (DIM == 3) ok = ok && make_window<ORDER, W, R>(n1, m1, wy);
+    if (!ok) return false;
+    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    double* Jx = sJ;
+    double* Jy = sJ + P.j_stride;
+    double* Jz = sJ + 2 * P.j_stride;
+    const R half = A::c(0.5), k12 = A::c(1.0 / 12.0);
+    R Ax[W], Az[W], Dx12[W], Dz12[W];
+#pragma unroll
+    for (int l = 0; l < W; ++l) {
+        Ax[l] = fma(half, wx.DS[l], wx.S0[l]);
+        Az[l] = fma(half, wz.DS[l], wz.S0[l]);
+        Dx12[l] = k12 * wx.DS[l];
+        Dz12[l] = k12 * wz.DS[l];
+    }
+    if constexpr (DIM == 3) {
+        R Ay[W];
+#pragma unroll
+        for (int l = 0; l < W; ++l) Ay[l] = fma(half, wy.DS[l], wy.S0[l]);
+        const int bx = wx.base + lo, by = wy.base + lo, bz = wz.base + lo;
+        {
+            const R c = qw * jf[0];
+            R Pf[W - 1];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc = acc + wx.DS[l]; Pf[l] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const R T = fma(Ay[j], Az[k], wy.DS[j] * Dz12[k]);
+                    double* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
+#pragma unroll
+                    for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * T);
+                }
+        }
+        {
+            const R c = qw * jf[1];
+            R Pf[W - 1];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int j = 0; j < W - 1; ++j) { acc = acc + wy.DS[j]; Pf[j] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const R T = fma(Ax[i], Az[k], wx.DS[i] * Dz12[k]);
+                    double* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
+#pragma unroll
+                    for (int j = 0; j < W - 1; ++j) jadd(col + j * jx, Pf[j] * T);
+                }
+        }
+        {
+            const R c = qw * jf[2];
+            R Pf[W - 1];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) { acc = acc + wz.DS[k]; Pf[k] = c * acc; }
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const R T = fma(Ax[i], Ay[j], Dx12[i] * wy.DS[j]);
+                    double* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
+#pragma unroll
+                    for (int k = 0; k < W - 1; ++k) jadd(col + k * jx * jy, Pf[k] * T);
+                }
+        }
+    } else {
+        const int bx = wx.base + lo, bz = wz.base + lo;
+        {  // Jx(i,k) = -(q w /(dz dt)) sum_{i'<=i} DSx(i') (S0z + DSz/2)
+            const R c = qw * jf[0];
+            R Pf[W - 1];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int l = 0; l < W - 1; ++l) { acc = acc + wx.DS[l]; Pf[l] = c * acc; }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                double* row = Jx + (bz + k) * jx + bx;
+#pragma unroll
+                for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * Az[k]);
+            }
+        }
+        {
+            const R c = qw * jf[2];
+            R Pf[W - 1];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) { acc = acc + wz.DS[k]; Pf[k] = c * acc; }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                double* col = Jz + bz * jx + (bx + i);
+#pragma unroll
+                for (int k = 0; k < W - 1; ++k) jadd(col + k * jx, Pf[k] * Ax[i]);
+            }
+        }
+        {  // out-of-plane Jy = q w vy / (dx dz) * (Ax Az + DSx DSz / 12)
+            const R c = qw * vy * jf[1];
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    jadd(Jy + (bz + k) * jx + (bx + i), c * fma(Ax[i], Az[k], Dx12[i] * wz.DS[k]));
+        }
+    }
+    return true;
+}
+
+// Linear shapes, particle keeping its cell in every direction: the window is
+// the two nodes of the cell, DS = (-d, d) with d = f1 - f0, so the prefix sum
+// has one term and the transverse weight A_a A_b + DS_a DS_b / 12 is
+// A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
+// deposit<R, DIM, 1, 2>, with fewer instructions.
+template <class R, int DIM>
+__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __restrict__ sJ,
+                                                   const SmemPlan& P, R qw, R vy, const R* jf,
+                                                   const Support<1, R>* n, const Support<1, R>* m) {
+    using A = Arith<R>;
+    const R k12 = A::c(1.0 / 12.0), half = A::c(0.5), one = A::c(1.0);
+    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    double* Jx = sJ;
+    double* Jy = sJ + P.j_stride;
+    double* Jz = sJ + 2 * P.j_stride;
+    const R dx = m[0].w[1] - n[0].w[1], dz = m[2].w[1] - n[2].w[1];
+    const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
+    const R ax0 = one - mx, az0 = one - mz;
+    const int bx = n[0].s + lo, bz = n[2].s + lo;
+    if constexpr (DIM == 3) {
+        const R dy = m[1].w[1] - n[1].w[1];
+        const R my = fma(half, dy, n[1].w[1]);
+        const R ay0 = one - my;
+        const int by = n[1].s + lo;
+        {   // Jx at (bx, by + j, bz + k)
+            const R e = (dy * dz) * k12;
+            const R pf = -((qw * jf[0]) * dx);
+            double* r = Jx + (bz * jy + by) * jx + bx;
+            jadd(r, pf * fma(ay0, az0, e));
+            jadd(r + jx, pf * fma(my, az0, -e));
+            jadd(r + jx * jy, pf * fma(ay0, mz, -e));
+            jadd(r + jx * jy + jx, pf * fma(my, mz, e));
+        }
+        {   // Jy at (bx + i, by, bz + k)
+            const R e = (dx * dz) * k12;
+            const R pf = -((qw * jf[1]) * dy);
+            double* r = Jy + (bz * jy + by) * jx + bx;
+            jadd(r, pf * fma(ax0, az0, e));
+            jadd(r + 1, pf * fma(mx, az0, -e));
+            jadd(r + jx * jy, pf * fma(ax0, mz, -e));
+            jadd(r + jx * jy + 1, pf * fma(mx, mz, e));
+        }
+        {   // Jz at (bx + i, by + j, bz)
+            const R e = (dx * dy) * k12;
+            const R pf = -((qw * jf[2]) * dz);
+            double* r = Jz + (bz * jy + by) * jx + bx;
+            jadd(r, pf * fma(ax0, ay0, e));
+            jadd(r + 1, pf * fma(mx, ay0, -e));
+            jadd(r + jx, pf * fma(ax0, my, -e));
+            jadd(r + jx + 1, pf * fma(mx, my, e));
+        }
+    } else {
+        {   // Jx at (bx, bz + k): -(q w/(dz dt)) DSx A_z
+            const R pf = -((qw * jf[0]) * dx);
+            double* r = Jx + bz * jx + bx;
+            jadd(r, pf * az0);
+            jadd(r + jx, pf * mz);
+        }
+        {   // Jz at (bx + i, bz)
+            const R pf = -((qw * jf[2]) * dz);
+            double* r = Jz + bz * jx + bx;
+            jadd(r, pf * ax0);
+            jadd(r + 1, pf * mx);
+        }
+        {   // out-of-plane Jy at (bx + i, bz + k)
+            const R e = (dx * dz) * k12;
+            const R c = qw * vy * jf[1];
+            double* r = Jy + bz * jx + bx;
+            jadd(r, c * fma(ax0, az0, e));
+            jadd(r + 1, c * fma(mx, az0, -e));
+            jadd(r + jx, c * fma(ax0, mz, -e));
+            jadd(r + jx + 1, c * fma(mx, mz, e));
+        }
+    }
+}
+
+// Gather, Boris push, and deposit of one particle.  Particles that keep their
+// support in every direction deposit at once on the small window; the others
+// go to the warp's ring buffer, drained 32 at a time by drain_warp.
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
+                                         const R* __restrict__ sEB, double* __restrict__ sJ,
+                                         double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
+                                         const R* jf, const R* dtd, R kq, int64_t p, int32_t* err) {
+    using A = Arith<R>;
+    double X = sp.cur[0][p], Z = sp.cur[2][p];
+    double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
+    const R u0 = A::from(sp.cur[3][p]), u1 = A::from(sp.cur[4][p]), u2 = A::from(sp.cur[5][p]);
+    const double w = sp.cur[6][p];
+
+    const double xl = X - (double)tl.o[0];
+    const double yl = (DIM == 3) ? Y - (double)tl.o[1] : 0.0;
+    const double zl = Z - (double)tl.o[2];
+
+    // ---- gather at x^n: node and half-node supports per direction
+    Support<ORDER, R> nd[3], hf[3];
+    supports<ORDER, R>(xl, nd[0], hf[0]);
+    supports<ORDER, R>(zl, nd[2], hf[2]);
+    if (DIM == 3) {
+        supports<ORDER, R>(yl, nd[1], hf[1]);
+    } else {
+        nd[1].s = -1;
+        nd[1].w[0] = A::c(1.0);
+        hf[1] = nd[1];
+    }
+    {
+        // the particle must sit in its tile (local cell index in [0, T))
+        bool in;
+        if (ORDER == 1) {  // node support start = floor(xl)
+            in = nd[0].s >= 0 && nd[0].s < S.T[0] && nd[2].s >= 0 && nd[2].s < S.T[2];
+            if (DIM == 3) in = in && nd[1].s >= 0 && nd[1].s < S.T[1];
+        } else if (ORDER == 3) {  // node support start = floor(xl) - 1
+            in = nd[0].s >= -1 && nd[0].s < S.T[0] - 1 && nd[2].s >= -1 && nd[2].s < S.T[2] - 1;
+            if (DIM == 3) in = in && nd[1].s >= -1 && nd[1].s < S.T[1] - 1;
+        } else {  // quadratic: half-node support start = floor(xl) - 1
+            in = hf[0].s >= -1 && hf[0].s < S.T[0] - 1 && hf[2].s >= -1 && hf[2].s < S.T[2] - 1;
+            if (DIM == 3) in = in && hf[1].s >= -1 && hf[1].s < S.T[1] - 1;
+        }
+        if (!in) {
+            atomicOr(err, PIC_DERR_BOUNDS);
+            sp.key[p] = S.ntiles;
+            warp_hist_add(sp.count, S.ntiles);
+            return;
+        }
+    }
+    const int SX = S.ebs[0], SY = S.ebs[1];
+    const R* Ex = sEB;
+    const R* Ey = sEB + P.eb_stride;
+    const R* Ez = sEB + 2 * P.eb_stride;
+    const R* Bx = sEB + 3 * P.eb_stride;
+    const R* By = sEB + 4 * P.eb_stride;
+    const R* Bz = sEB + 5 * P.eb_stride;
+    const R e0 = interp<R, ORDER, DIM>(Ex, SX, SY, hf[0], nd[1], nd[2]);
+    const R e1 = interp<R, ORDER, DIM>(Ey, SX, SY, nd[0], hf[1], nd[2]);
+    const R e2 = interp<R, ORDER, DIM>(Ez, SX, SY, nd[0], nd[1], hf[2]);
+    const R b0 = interp<R, ORDER, DIM>(Bx, SX, SY, nd[0], hf[1], hf[2]);
+    const R b1 = interp<R, ORDER, DIM>(By, SX, SY, hf[0], nd[1], hf[2]);
+    const R b2 = interp<R, ORDER, DIM>(Bz, SX, SY, hf[0], hf[1], nd[2]);
+
+    // ---- relativistic Boris push
+    const R one = A::c(1.0);
+    const R m0 = fma(kq, e0, u0), m1 = fma(kq, e1, u1), m2 = fma(kq, e2, u2);
+    const R ig = A::rsqrt(fma(m2, m2, fma(m1, m1, fma(m0, m0, one))));
+    const R kg = kq * ig;
+    const R t0 = kg * b0, t1 = kg * b1, t2 = kg * b2;
+    const R t2n = fma(t2, t2, fma(t1, t1, t0 * t0));
+    const R sf = A::two_over(one + t2n);
+    const R s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
+    const R d0 = m0 + (m1 * t2 - m2 * t1);
+    const R d1 = m1 + (m2 * t0 - m0 * t2);
+    const R d2 = m2 + (m0 * t1 - m1 * t0);
+    const R p0 = m0 + (d1 * s2 - d2 * s1);
+    const R p1 = m1 + (d2 * s0 - d0 * s2);
+    const R p2 = m2 + (d0 * s1 - d1 * s0);
+    const R n0 = fma(kq, e0, p0), n1 = fma(kq, e1, p1), n2 = fma(kq, e2, p2);
+    const R ign = A::rsqrt(fma(n2, n2, fma(n1, n1, fma(n0, n0, one))));
+    const R v1 = n1 * ign;
+    const double dX = A::to((n0 * ign) * dtd[0]), dZ = A::to((n2 * ign) * dtd[2]);
+    const double dY = (DIM == 3) ? A::to(v1 * dtd[1]) : 0.0;
+
+    // ---- Esirkepov deposit of J^{n+1/2} from x^n to x^{n+1}
+    Support<ORDER, R> mv[3];
+    mv[0] = support<ORDER, R>(xl + dX);
+    mv[2] = support<ORDER, R>(zl + dZ);
+    if (DIM == 3) mv[1] = support<ORDER, R>(yl + dY);
+    else mv[1] = nd[1];
+    const R qw = A::from(sp.q * w);
+    bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
+    if (same) {
+        if constexpr (ORDER == 1)
+            deposit_lin_incell<R, DIM>(S, sJ, P, qw, v1, jf, nd, mv);
+        else
+            deposit<R, DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, jf, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
+    } else {
+        // the ring never holds more than 31 + 32 entries: the warp drains 32
+        // whenever 32 are waiting
+        const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
+        sQw[0 * WQ + slot] = xl;
+        sQw[1 * WQ + slot] = zl;
+        sQw[2 * WQ + slot] = dX;
+        sQw[3 * WQ + slot] = dZ;
+        sQw[4 * WQ + slot] = sp.q * w;
+        sQw[5 * WQ + slot] = DIM == 3 ? yl : A::to(v1);
+        if (DIM == 3) sQw[6 * WQ + slot] = dY;
+    }
+
+    // ---- new position, boundary, re-sort key
+    const double nxd = (double)S.n[0], nyd = (double)S.n[1], nzd = (double)S.n[2];
+    X += dX;
+    Z += dZ;
+    if (is_neg(X)) X += nxd;
+    if (ge_pos(X, nxd)) X -= nxd;
+    if (DIM == 3) {
+        Y += dY;
+        if (is_neg(Y)) Y += nyd;
+        if (ge_pos(Y, nyd)) Y -= nyd;
+    }
+    int key;
+    if (S.absorb > 0) {
+        if (Z < (double)S.absorb || Z >= (double)(S.n[2] - S.absorb)) key = S.ntiles;
+        else key = -1;
+    } else {
+        if (is_neg(Z)) Z += nzd;
+        if (ge_pos(Z, nzd)) Z -= nzd;
+        key = -1;
+    }
+    if (key < 0) {
+        int ix = min(max(ifloor(X), 0), S.n[0] - 1);
+        int iy = (DIM == 3) ? min(max(ifloor(Y), 0), S.n[1] - 1) : 0;
+        int iz = min(max(ifloor(Z), 0), S.n[2] - 1);
+        key = tile_key(S, ix, iy, iz);
+    }
+    sp.cur[0][p] = X;
+    if (DIM == 3) sp.cur[1][p] = Y;
+    sp.cur[2][p] = Z;
+    sp.cur[3][p] = A::to(n0);
+    sp.cur[4][p] = A::to(n1);
+    sp.cur[5][p] = A::to(n2);
+    sp.key[p] = key;
+    warp_hist_add(sp.count, key);
+}
+
+// A warp deposits n <= 32 queued (cell-crossing) particles of its ring,
+// starting at slot head, on the ORDER + 2 window: lane i takes entry head + i.
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ void drain_warp(const SimDev& S, double* __restrict__ sJ,
+                                           const double* __restrict__ sQw, unsigned head, unsigned n,
+                                           const SmemPlan& P, const R* jf, int32_t* err) {
+    using A = Arith<R>;
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane >= n) return;
+    const unsigned i = (head + lane) & (WQ - 1);
+    const double xl = sQw[0 * WQ + i], zl = sQw[1 * WQ + i];
+    const double dX = sQw[2 * WQ + i], dZ = sQw[3 * WQ + i], qw = sQw[4 * WQ + i];
+    const double yl = DIM == 3 ? sQw[5 * WQ + i] : 0.0, vy = DIM == 3 ? 0.0 : sQw[5 * WQ + i];
+    const double dY = DIM == 3 ? sQw[6 * WQ + i] : 0.0;
+    Support<ORDER, R> nd[3], mv[3];
+    nd[0] = support<ORDER, R>(xl);
+    nd[2] = support<ORDER, R>(zl);
+    mv[0] = support<ORDER, R>(xl + dX);
+    mv[2] = support<ORDER, R>(zl + dZ);
+    if (DIM == 3) {
+        nd[1] = support<ORDER, R>(yl);
+        mv[1] = support<ORDER, R>(yl + dY);
+    } else {
+        nd[1].s = -1;
+        nd[1].w[0] = A::c(1.0);
+        mv[1] = nd[1];
+    }
+    if (!deposit<R, DIM, ORDER, ORDER + 2>(S, sJ, P, A::from(qw), A::from(vy), jf, nd[0], nd[1], nd[2],
+                                           mv[0], mv[1], mv[2]))
+        atomicOr(err, PIC_DERR_BOUNDS);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// MINB = resident CTAs per SM the register allocation is sized for (1: up to
+// 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM).
+// PREC = arithmetic of the particle push: 0 FP64, 1 float-float (storage,
+// positions, index math and the shared J atomics stay FP64 in both).
+template <int DIM, int ORDER, int MINB, int PREC>
+__global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
+                                                              SimDev* __restrict__ sims) {
+    using R = typename std::conditional<PREC == 1, dd, double>::type;
+    using A = Arith<R>;
+    extern __shared__ __align__(128) double smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    // TMA destinations must be 128-byte aligned: round the dynamic base up
+    double* smem = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    __shared__ int s_unit, s_list, s_abort;
+    __shared__ unsigned s_qhead[QMAXWARPS], s_qtail[QMAXWARPS];
+    __shared__ unsigned long long s_cost;
+
+    const int nlists = sd->meta[0];
+    const int steal = sd->meta[1];
+    const int my_list = blockIdx.x % nlists;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        s_list = my_list;
+        s_abort = 0;
+        for (int w = 0; w < QMAXWARPS; ++w) s_qhead[w] = s_qtail[w] = 0u;
+        s_cost = 0ull;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    Tile cur;
+    cur.sim = -1;
+    cur.t = -1;
+    int visited = 0;
+
+    while (true) {
+        if (threadIdx.x == 0) {
+            int u = -1;
+            while (visited < nlists) {
+                int L = s_list;
+                int pos = atomicAdd(sd->head + L, 1);
+                int b = sd->list_off[L], e = sd->list_off[L + 1];
+                if (b + pos < e) { u = b + pos; break; }
+                if (!steal) { visited = nlists; break; }
+                s_list = (L + 1) % nlists;
+                ++visited;
+            }
+            s_unit = u;
+        }
+        __syncthreads();
+        const int u = s_unit;
+        if (u < 0) break;
+        const UnitDev unit = sd->units[u];
+        const SimDev& S = sims[unit.sim];
+        const uint64_t t_unit0 = threadIdx.x == 0 ? globaltimer() : 0ull;
+        const SmemPlan P = smem_plan(S.ebs, S.js);
+        double* sEBd = smem;
+        const R* sEB = reinterpret_cast<const R*>(smem);
+        double* sJ = smem + 6 * P.eb_stride;
+        unsigned long long my_clk = 0ull;
+        // the simulation's constants in R
+        const R jf[3] = {A::from(S.jfac[0]), A::from(DIM == 3 ? S.jfac[1] : S.jyfac2d), A::from(S.jfac[2])};
+        const R dtd[3] = {A::from(S.dtd[0]), A::from(S.dtd[1]), A::from(S.dtd[2])};
+
+        for (int spi = 0; spi < S.nsp; ++spi) {
+            const SpeciesDev& sp = S.sp[spi];
+            const R kq = A::from(sp.kq);
+            const int t_first = unit.box * S.tiles_per_box;
+            const int t_end = t_first + S.tiles_per_box;
+            const int64_t b0 = sp.off[t_first], nbp = sp.off[t_end] - b0;
+            const int64_t r0 = b0 + (nbp * unit.chunk) / unit.nchunks;
+            const int64_t r1 = b0 + (nbp * (unit.chunk + 1)) / unit.nchunks;
+            if (r0 >= r1) continue;
+            for (int t = t_first; t < t_end; ++t) {
+                const int64_t s0 = max(sp.off[t], r0), s1 = min(sp.off[t + 1], r1);
+                if (s0 >= s1) continue;
+                if (t != cur.t || unit.sim != cur.sim) {
+                    __syncthreads();
+                    if (cur.t >= 0) {
+                        const SimDev& CS = sims[cur.sim];
+                        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
+                        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+                        __syncthreads();
+                    }
+                    cur.sim = unit.sim;
+                    cur.t = t;
+                    tile_origin(S, t, cur.o);
+                    if (threadIdx.x == 0) {
+                        fence_proxy_async();
+                        mbar_expect_tx(&bar, (uint32_t)(6 * P.eb_vol * sizeof(double)));
+                        constexpr int H = EBHalo<ORDER>::lo;
+                        const int x0 = cur.o[0] - H + S.g[0];
+                        const int y0 = (DIM == 3) ? cur.o[1] - H + S.g[1] : 0;
+                        const int z0 = cur.o[2] - H + S.g[2];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c)
+                            tma_load_3d(sEBd + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
+                    }
+                    for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJ[i] = 0.0;
+                    bool ok = mbar_wait_bounded(&bar, phase);
+                    phase ^= 1u;
+                    if (!ok) {
+                        atomicOr(sd->err, PIC_DERR_TMA_TIMEOUT);
+                        atomicExch(&s_abort, 1);
+                    }
+                    __syncthreads();
+                    if (s_abort) {
+                        // the copies may still be in flight: one more bounded wait, then leave
+                        if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase ^ 1u);
+                        __syncthreads();
+                        return;
+                    }
+                    if constexpr (PREC == 1) {
+                        // E/B tile to float pairs, in place (8 bytes either way)
+                        for (int i = threadIdx.x; i < 6 * P.eb_stride; i += blockDim.x) {
+                            const dd v = dd_from(sEBd[i]);
+                            reinterpret_cast<dd*>(sEBd)[i] = v;
+                        }
+                        __syncthreads();
+                    }
+                }
+                const unsigned long long c0 = clock64();
+                {
+                    // per-warp loop: no CTA barrier until the tile changes
+                    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                    double* sQw = sJ + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
+                    volatile unsigned* vtail = s_qtail + warp;
+                    for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
+                        const int64_t p = p0 + lane;
+                        if (p < s1)
+                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, sJ, sQw, s_qtail + warp, P, jf, dtd, kq, p,
+                                                    sd->err);
+                        __syncwarp();
+                        const unsigned head = s_qhead[warp], tail = *vtail;
+                        if (tail - head >= 32u) {
+                            drain_warp<R, DIM, ORDER>(S, sJ, sQw, head, 32u, P, jf, sd->err);
+                            __syncwarp();
+                            if (lane == 0) s_qhead[warp] = head + 32u;
+                            __syncwarp();
+                        }
+                    }
+                    __syncwarp();
+                    const unsigned head = s_qhead[warp], tail = *vtail;
+                    if (tail != head) {
+                        drain_warp<R, DIM, ORDER>(S, sJ, sQw, head, tail - head, P, jf, sd->err);
+                        __syncwarp();
+                        if (lane == 0) s_qhead[warp] = tail;
+                    }
+                    __syncwarp();
+                }
+                my_clk += clock64() - c0;
+            }
+        }
+        // in-situ cost: thread clocks -> warp sum -> shared -> one global add per unit
+        unsigned long long ws = warp_sum_u64(my_clk);
+        if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&s_cost, ws);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cost) atomicAdd((unsigned long long*)(S.cost_clock + unit.box), s_cost);
+            s_cost = 0ull;
+            // kernel-time cost: wall span of the unit on this CTA (ns)
+            atomicAdd((unsigned long long*)(S.cost_time + unit.box),
+                      (unsigned long long)(globaltimer() - t_unit0));
+        }
+    }
+    if (cur.t >= 0) {
+        __syncthreads();
+        const SimDev& CS = sims[cur.sim];
+        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
+        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+    }
+}
+
+// ---- host side of one precision: launch, attributes, occupancy
+template <int DIM, int ORDER, int PREC>
+static cudaError_t launch_particles_t(const LaunchCfg& cfg, size_t smem, const SchedDev* sched,
+                                      SimDev* sims, cudaStream_t st) {
+    if (cfg.minb == 2)
+        pic_particle_kernel<DIM, ORDER, 2, PREC><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    else
+        pic_particle_kernel<DIM, ORDER, 1, PREC><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    return cudaGetLastError();
+}
+
+template <int DIM, int ORDER, int PREC>
+static cudaError_t prepare_t(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 1, PREC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 2, PREC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int DIM, int ORDER, int PREC>
+static int occupancy_t(int minb, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e = minb == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, pic_particle_kernel<DIM, ORDER, 2, PREC>, threads, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, pic_particle_kernel<DIM, ORDER, 1, PREC>, threads, smem);
+    return e == cudaSuccess ? n : 0;
+}
+
+// dispatch over (dim, order) for one precision
+#define PIC_DISPATCH_DO(FN, ...)                                         \
+    do {                                                                 \
+        if (dim == 3 && order == 1) return FN<3, 1, PIC_PREC>(__VA_ARGS__); \
+        if (dim == 3 && order == 2) return FN<3, 2, PIC_PREC>(__VA_ARGS__); \
+        if (dim == 3 && order == 3) return FN<3, 3, PIC_PREC>(__VA_ARGS__); \
+        if (dim == 2 && order == 1) return FN<2, 1, PIC_PREC>(__VA_ARGS__); \
+        if (dim == 2 && order == 2) return FN<2, 2, PIC_PREC>(__VA_ARGS__); \
+        if (dim == 2 && order == 3) return FN<2, 3, PIC_PREC>(__VA_ARGS__); \
+    } while (0)
+
+}  // namespace

@@ -1,0 +1,33 @@
+// pic_particles_f64.cu -- FP64 instantiation of the particle kernel, and the
+// shared-memory size of its tiles.
+#define PIC_PREC 0
+#include "pic_particle_kernel.cuh"
+
+cudaError_t pic_launch_particles_p0(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                        const SchedDev* sched, SimDev* sims, cudaStream_t st) {
+    PIC_DISPATCH_DO(launch_particles_t, cfg, smem, sched, sims, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t pic_prepare_particles_p0(int dim, int order, size_t smem) {
+    PIC_DISPATCH_DO(prepare_t, smem);
+    return cudaErrorInvalidValue;
+}
+
+int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t smem) {
+    PIC_DISPATCH_DO(occupancy_t, minb, threads, smem);
+    return 0;
+}
+
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads) {
+    int ebs[3], js[3];
+    for (int a = 0; a < 3; ++a) {
+        bool act = !(dim == 2 && a == 1);
+        ebs[a] = act ? T[a] + (order == 1 ? 2 : order == 2 ? 3 : 4) : 1;
+        js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
+    }
+    if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
+    // tiles + one crossing ring per warp + alignment slack of the dynamic base
+    const int qf = dim == 3 ? QFields<3>::n : QFields<2>::n;
+    return smem_plan(ebs, js).bytes + (size_t)(threads / 32) * qf * WQ * sizeof(double) + 128;
+}

@@ -267,7 +267,7 @@ pic_status rebuild_units(pic_server* s) {
     SCU(s, cudaStreamSynchronize(s->stream));
     if (!s->active_slots.empty()) {
         SCU(s, pic_prepare_particles(s->desc.dim, s->desc.shape_order, s->smem));
-        int per_sm = pic_particle_occupancy(s->desc.dim, s->desc.shape_order, 1, s->threads, s->smem);
+        int per_sm = pic_particle_occupancy(s->desc.dim, s->desc.shape_order, 1, s->threads, s->smem, 0);
         s->ctas = s->nsm * std::max(1, std::min(per_sm, 2));
     }
     s->dirty = false;
@@ -400,7 +400,7 @@ pic_status pic_server_tick(pic_server* s, int* n_active, int* n_pending) {
     const int na = (int)s->active_slots.size();
     if (na > 0) {
         SCU(s, pic_launch_zero_j_multi(s->d_sims, s->d_slots, na, s->max_padded, s->stream));
-        LaunchCfg cfg{s->threads, s->ctas, 1};
+        LaunchCfg cfg{s->threads, s->ctas, 1, 0};
         SCU(s, pic_launch_particles(s->desc.dim, s->desc.shape_order, cfg, s->smem, s->ds, s->d_sims, s->stream));
         SCU(s, pic_launch_fields_multi(s->d_sims, s->d_slots, na, s->desc.dim, s->max_cells, s->max_padded,
                                        false, s->stream));

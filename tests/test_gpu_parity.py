@@ -246,3 +246,45 @@ def test_bin_particles_empty_and_errors():
     assert off.cpu().tolist() == [0, 0, 0, 0, 0]
     with pytest.raises(L.PicError):
         S.bin_particles(3, (8, 8, 8), (3, 4, 8), (1, 1, 1), z, z, z, off, perm)
+
+
+FF_CASES = [
+    (3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1),
+    (3, (24, 16, 16), (8, 8, 16), (0.3, 0.35, 0.4), 2),
+    (3, (16, 16, 24), (8, 8, 8), (0.3, 0.3, 0.35), 3),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.35), 1),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.3), 3),
+]
+
+
+@pytest.mark.parametrize("case", FF_CASES, ids=[f"{c[0]}d_o{c[4]}" for c in FF_CASES])
+def test_float_float_variant_parity(case):
+    """The mixed-precision variant (float-float particle push, FP64 storage,
+    positions and current sums) meets the same 1e-10 bar against the FP64
+    oracle after 10 steps."""
+    dim, n, box, dx, order = case
+    wl = workloads.random_plasma(500 + sum(n) + order, dim, n, box, dx, order, nspecies=2, npart=4000,
+                                 umax=2.0)
+    fields = workloads.random_fields(8, n, amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    sim.set_launch(precision=2)
+    assert sim.get_launch()["precision"] == 2
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+
+
+def test_float_float_variant_uniform32_and_laser():
+    wl = workloads.uniform32()
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(precision=2)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+    wl = workloads.random_plasma(77, 3, (16, 16, 48), (8, 8, 16), (0.3, 0.3, 0.3), 1, nspecies=2, npart=3000,
+                                 umax=3.0, absorb=6, laser=True)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(precision=2)
+    sim.step(12)
+    ref.step(12)
+    compare(sim, ref, wl)

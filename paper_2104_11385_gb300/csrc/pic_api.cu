@@ -610,6 +610,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     for (int a = 0; a < 3; ++a) {
         bool act = !(g.dim == 2 && a == 1);
         h.n[a] = (int)g.ncell[a];
+        h.nd[a] = (double)h.n[a];
         // x guard: even tile origin - E/B halo + guard must be even (TMA)
         h.g[a] = act ? (a == 0 ? (g.shape_order == 3 ? PIC_GX + 1 : PIC_GX) : PIC_G) : 0;
         h.pn[a] = h.n[a] + 2 * h.g[a];

@@ -4,8 +4,8 @@
 // Knuth's TwoSum and products the FMA-based TwoProd (Dekker 1971; Shewchuk
 // 1997; Hida, Li & Bailey's double-double with float limbs), so each operation
 // costs a handful of FP32 instructions instead of one FP64 instruction issued
-// at 1/64 of the FP32 rate on GB300.  Conversions between double and float run
-// at FP32 speed; only the split of a double needs one FP64 subtraction.
+// at 1/64 of the FP32 rate on GB300.  Conversions between double and float-
+// float work on the bit patterns with integer instructions.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -27,13 +27,78 @@ __device__ __forceinline__ dd dd_quick_two_sum(float a, float b) {  // |a| >= |b
 }
 
 // ---- conversions
+// double -> float-float by integer work on the IEEE-754 bits (every FP64
+// instruction, conversions included, issues at the FP64 rate): hi is x rounded
+// to 24 bits (ties away from zero on the magnitude), lo the remainder in units
+// of 2^(e-52), at most 2^28 of them, rounded to 24 bits by one int->float
+// conversion and scaled by adding to its exponent field.  |x - (hi + lo)| <=
+// 2^-49 |x|.  Magnitudes outside [2^-74, 2^127) (where lo would leave the
+// normal float range) take the two-conversion FP64 route; zero is exact.
 __device__ __forceinline__ dd dd_from(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long u = b & 0x7FFFFFFFFFFFFFFFull;
+    const int be = (int)(u >> 52);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    if (be >= 1023 - 74 && be <= 1023 + 126) {
+        const unsigned long long hb = (u + (1ull << 28)) >> 29;  // exponent | 23-bit mantissa
+        const float h = __uint_as_float(sgn | (unsigned)(hb - (896ull << 23)));
+        // the bit patterns are linear in the value with slope 2^(e-52) up to
+        // the binade above, so the pattern difference is the remainder
+        const int d = (int)(long long)(u - (hb << 29));
+        float l = 0.0f;
+        if (d != 0)
+            l = __uint_as_float((__float_as_uint(__int2float_rn(d)) + ((unsigned)(be - 1023 - 52) << 23)) ^ sgn);
+        return dd{h, l};
+    }
+    if (u == 0ull) return dd{__uint_as_float(sgn), 0.0f};
     const float h = __double2float_rn(x);
     return dd{h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double dd_to(dd a) { return (double)a.h + (double)a.l; }
+
+// float-float -> double by integer work: hi widened exactly (exponent rebias,
+// mantissa << 29), lo added in units of the double ulp of hi (truncated), with
+// the pattern arithmetic of dd_from; a hi that is a power of two and a lo of
+// the other sign land in the binade below, where the unit is half as large.
+// Needs |lo| <= 2^5 ulp_double(hi) (every normalised pair); other pairs, and a
+// hi or lo outside the normal float range, take the FP64 route.
+__device__ __forceinline__ double dd_to(dd a) {
+    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+    const int he = (int)((hb >> 23) & 0xFFu), le = (int)((lb >> 23) & 0xFFu);
+    if (he >= 1 && he <= 254) {
+        unsigned long long mag = ((unsigned long long)(hb & 0x7FFFFFFFu) + (896ull << 23)) << 29;
+        if ((lb & 0x7FFFFFFFu) != 0u) {
+            int sh = le - he + 29;
+            if (le == 0 || sh > 5) return (double)a.h + (double)a.l;
+            const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+            const bool sub = ((hb ^ lb) & 0x80000000u) != 0u;
+            if (sub && (hb & 0x7FFFFFu) == 0u) sh += 1;
+            const unsigned long long dl = sh >= 0 ? (ml << sh) : (sh > -25 ? (ml >> (-sh)) : 0ull);
+            mag = sub ? mag - dl : mag + dl;
+        }
+        return __longlong_as_double((long long)(mag | ((unsigned long long)(hb & 0x80000000u) << 32)));
+    }
+    return (double)a.h + (double)a.l;
+}
 __host__ __device__ constexpr dd dd_const(double x) {
     return dd{static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x)))};
+}
+
+// float-float -> double for a normalised pair (|lo| <= ulp(hi)/2), branch-
+// free: the form dd_to takes in the current deposit, where it runs dozens of
+// times per particle.  Float subnormals flush to zero (|hi| below 2^-126
+// gives 0, a subnormal lo is dropped: an absolute error below 2^-126).
+__device__ __forceinline__ double dd_to_norm(dd a) {
+    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+    const unsigned ha = hb & 0x7FFFFFFFu;
+    unsigned long long mag = ((unsigned long long)ha + (896ull << 23)) << 29;
+    const int sh0 = (int)((lb >> 23) & 0xFFu) - (int)(ha >> 23) + 29;
+    const bool sub = ((hb ^ lb) & 0x80000000u) != 0u;
+    const int sh = sh0 + ((sub && (ha & 0x7FFFFFu) == 0u) ? 1 : 0);
+    const unsigned long long ml = (lb & 0x7F800000u) ? (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u) : 0ull;
+    const unsigned long long dl = sh >= 0 ? (ml << sh) : (ml >> min(-sh, 63));
+    mag = sub ? mag - dl : mag + dl;
+    mag = (ha >= 0x00800000u) ? mag : 0ull;
+    return __longlong_as_double((long long)(mag | ((unsigned long long)(hb & 0x80000000u) << 32)));
 }
 
 // ---- arithmetic

@@ -70,6 +70,7 @@ struct SimDev {
     int js[3];            // J shared tile extents
     int jlo;              // J tile starts jlo cells below the tile origin
     double d[3];          // cell sizes
+    double nd[3];         // n as doubles (periodic wrap of positions)
     double dt;
     double dtd[3];        // dt / d
     double jfac[3];       // -1/(dA_perp dt) for the prefix currents (3D); 2D see kernel

@@ -167,7 +167,8 @@ __device__ __forceinline__ Support<ORDER, R> support(double xi) {
     } else if constexpr (ORDER == 2) {
         // nearest node c = floor(xi + 1/2), d = xi - c in [-1/2, 1/2)
         const bool up = ge_half(f);
-        const R d = A::from(up ? f - 1.0 : f);
+        const R fr = A::from(f);
+        const R d = up ? fr - A::c(1.0) : fr;
         const R a = A::c(0.5) - d, b = A::c(0.5) + d;
         r.s = i + (up ? 1 : 0) - 1;
         r.w[0] = A::c(0.5) * (a * a);
@@ -217,6 +218,21 @@ __device__ __forceinline__ void supports(double xi, Support<ORDER, R>& nd, Suppo
         hf.s = (up ? i : i - 1) - 1;
         cubic_weights<R>(g, hf.w);
     }
+}
+
+// supports relative to a tile origin o, from the global position: floor and
+// fraction of x are those of x - o (o an integer), without forming x - o
+template <int ORDER, class R>
+__device__ __forceinline__ Support<ORDER, R> support_at(double x, int o) {
+    Support<ORDER, R> r = support<ORDER, R>(x);
+    r.s -= o;
+    return r;
+}
+template <int ORDER, class R>
+__device__ __forceinline__ void supports_at(double x, int o, Support<ORDER, R>& nd, Support<ORDER, R>& hf) {
+    supports<ORDER, R>(x, nd, hf);
+    nd.s -= o;
+    hf.s -= o;
 }
 
 // E/B tile halo below the tile origin: 1 cell (orders 1, 2), 2 cells (order 3)
@@ -276,6 +292,49 @@ __device__ __forceinline__ R interp(const R* __restrict__ F, int SX, int SY, con
             acc = (c == 0) ? sz.w[0] * r : fma(sz.w[c], r, acc);
         }
         return acc;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T pick3(int a, const T& v0, const T& v1, const T& v2) {
+    return a == 0 ? v0 : (a == 1 ? v1 : v2);
+}
+
+// The six E/B components at one particle.  E_a sits on the half-node grid
+// along a and on nodes across it, B_a the other way round.  FP64 unrolls the
+// six interpolations; float-float runs them as a loop (its operations are
+// 7-11 FP32 instructions each, and six unrolled copies overflow the
+// instruction cache).
+template <class R, int ORDER, int DIM>
+__device__ __forceinline__ void gather6(const R* __restrict__ sEB, int stride, int SX, int SY,
+                                        const Support<ORDER, R>* nd, const Support<ORDER, R>* hf, R* e,
+                                        R* b) {
+    if constexpr (std::is_same<R, double>::value) {
+        e[0] = interp<R, ORDER, DIM>(sEB, SX, SY, hf[0], nd[1], nd[2]);
+        e[1] = interp<R, ORDER, DIM>(sEB + stride, SX, SY, nd[0], hf[1], nd[2]);
+        e[2] = interp<R, ORDER, DIM>(sEB + 2 * stride, SX, SY, nd[0], nd[1], hf[2]);
+        b[0] = interp<R, ORDER, DIM>(sEB + 3 * stride, SX, SY, nd[0], hf[1], hf[2]);
+        b[1] = interp<R, ORDER, DIM>(sEB + 4 * stride, SX, SY, hf[0], nd[1], hf[2]);
+        b[2] = interp<R, ORDER, DIM>(sEB + 5 * stride, SX, SY, hf[0], hf[1], nd[2]);
+    } else {
+        R v0 = Arith<R>::c(0.0), v1 = v0, v2 = v0, v3 = v0, v4 = v0, v5 = v0;
+#pragma unroll 1
+        for (int c = 0; c < 6; ++c) {
+            const int a = c < 3 ? c : c - 3;
+            const bool isb = c >= 3;
+            const Support<ORDER, R> sx = ((a == 0) != isb) ? hf[0] : nd[0];
+            const Support<ORDER, R> sy = ((a == 1) != isb) ? hf[1] : nd[1];
+            const Support<ORDER, R> sz = ((a == 2) != isb) ? hf[2] : nd[2];
+            const R v = interp<R, ORDER, DIM>(sEB + c * stride, SX, SY, sx, sy, sz);
+            v0 = c == 0 ? v : v0;
+            v1 = c == 1 ? v : v1;
+            v2 = c == 2 ? v : v2;
+            v3 = c == 3 ? v : v3;
+            v4 = c == 4 ? v : v4;
+            v5 = c == 5 ? v : v5;
+        }
+        e[0] = v0; e[1] = v1; e[2] = v2;
+        b[0] = v3; b[1] = v4; b[2] = v5;
     }
 }
 
@@ -350,7 +409,8 @@ __device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
 // slots per warp, up to 8 warps).
 constexpr int WQ = 64;
 constexpr int QMAXWARPS = 8;
-// queue fields: 0 xl, 1 zl, 2 dX, 3 dZ, 4 qw, 5 yl (3D) or vy (2D), 6 dY (3D)
+// queue fields: 0 x^n, 1 z^n, 2 x^{n+1}, 3 z^{n+1} (global, unwrapped), 4 q w,
+// 5 y^n (3D) or vy (2D), 6 y^{n+1} (3D)
 template <int DIM>
 struct QFields {
     static constexpr int n = DIM == 3 ? 7 : 6;
@@ -390,11 +450,10 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restric
 }
 
 
-// shared-memory J atomics take doubles; a float-float value is merged first
-template <class R>
-__device__ __forceinline__ void jadd(double* p, R v) {
-    atomicAdd(p, Arith<R>::to(v));
-}
+// shared-memory J atomics take doubles; a float-float value (a product,
+// hence normalised) is merged first
+__device__ __forceinline__ void jadd(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void jadd(double* p, dd v) { atomicAdd(p, dd_to_norm(v)); }
 
 // Esirkepov deposit of one particle into the shared J tile on windows of W
 // nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
@@ -425,7 +484,54 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
         Dx12[l] = k12 * wx.DS[l];
         Dz12[l] = k12 * wz.DS[l];
     }
-    if constexpr (DIM == 3) {
+    if constexpr (DIM == 3 && !std::is_same<R, double>::value) {
+        // float-float: one loop over the three currents (prefix axis a,
+        // transverse axes b < c), to keep the code small
+        R Ay[W], Dy12[W];
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            Ay[l] = fma(half, wy.DS[l], wy.S0[l]);
+            Dy12[l] = k12 * wy.DS[l];
+        }
+        const int sxy = jx * jy;
+        double* origin = sJ + ((wz.base + lo) * jy + (wy.base + lo)) * jx + (wx.base + lo);
+#pragma unroll 1
+        for (int a = 0; a < 3; ++a) {
+            const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+            const int sa = pick3(a, 1, jx, sxy), sb = pick3(b, 1, jx, sxy), sc = pick3(c, 1, jx, sxy);
+            const R cf = qw * pick3(a, jf[0], jf[1], jf[2]);
+            R Pf[W - 1], Ab[W], Ac[W], Db[W], Dc12[W];
+            R acc = A::c(0.0);
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+                if (l < W - 1) {
+                    acc = acc + pick3(a, wx.DS[l], wy.DS[l], wz.DS[l]);
+                    Pf[l] = cf * acc;
+                }
+                Ab[l] = b == 0 ? Ax[l] : Ay[l];
+                Db[l] = b == 0 ? wx.DS[l] : wy.DS[l];
+                Ac[l] = c == 1 ? Ay[l] : Az[l];
+                Dc12[l] = c == 1 ? Dy12[l] : Dz12[l];
+            }
+            double* Ja = origin + a * P.j_stride;
+#pragma unroll 1
+            for (int k = 0; k < W; ++k) {
+                R ack = Ac[0], dck = Dc12[0];
+#pragma unroll
+                for (int q = 1; q < W; ++q) {
+                    ack = k == q ? Ac[q] : ack;
+                    dck = k == q ? Dc12[q] : dck;
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const R T = fma(Ab[j], ack, Db[j] * dck);
+                    double* row = Ja + k * sc + j * sb;
+#pragma unroll
+                    for (int l = 0; l < W - 1; ++l) jadd(row + l * sa, Pf[l] * T);
+                }
+            }
+        }
+    } else if constexpr (DIM == 3) {
         R Ay[W];
 #pragma unroll
         for (int l = 0; l < W; ++l) Ay[l] = fma(half, wy.DS[l], wy.S0[l]);
@@ -537,7 +643,30 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
     const int bx = n[0].s + lo, bz = n[2].s + lo;
-    if constexpr (DIM == 3) {
+    if constexpr (DIM == 3 && !std::is_same<R, double>::value) {
+        // float-float: one loop over the three currents (axis a, transverse b < c)
+        const R dy = m[1].w[1] - n[1].w[1];
+        const R my = fma(half, dy, n[1].w[1]);
+        const R ay0 = one - my;
+        const int by = n[1].s + lo;
+        const int sxy = jx * jy;
+        double* origin = sJ + (bz * jy + by) * jx + bx;
+#pragma unroll 1
+        for (int a = 0; a < 3; ++a) {
+            const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+            const int sb = pick3(b, 1, jx, sxy), sc = pick3(c, 1, jx, sxy);
+            const R db = b == 0 ? dx : dy, dc = c == 1 ? dy : dz;
+            const R mb = b == 0 ? mx : my, mc = c == 1 ? my : mz;
+            const R ab = b == 0 ? ax0 : ay0, ac = c == 1 ? ay0 : az0;
+            const R e = (db * dc) * k12;
+            const R pf = -((qw * pick3(a, jf[0], jf[1], jf[2])) * pick3(a, dx, dy, dz));
+            double* r = origin + a * P.j_stride;
+            jadd(r, pf * fma(ab, ac, e));
+            jadd(r + sb, pf * fma(mb, ac, -e));
+            jadd(r + sc, pf * fma(ab, mc, -e));
+            jadd(r + sb + sc, pf * fma(mb, mc, e));
+        }
+    } else if constexpr (DIM == 3) {
         const R dy = m[1].w[1] - n[1].w[1];
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
@@ -601,23 +730,19 @@ template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
                                          const R* __restrict__ sEB, double* __restrict__ sJ,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
-                                         const R* jf, const R* dtd, R kq, int64_t p, int32_t* err) {
+                                         const R* jf, const R* dtd, R kq, R qs, int64_t p, int32_t* err) {
     using A = Arith<R>;
     double X = sp.cur[0][p], Z = sp.cur[2][p];
     double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
     const R u0 = A::from(sp.cur[3][p]), u1 = A::from(sp.cur[4][p]), u2 = A::from(sp.cur[5][p]);
-    const double w = sp.cur[6][p];
+    const R qw = qs * A::from(sp.cur[6][p]);
 
-    const double xl = X - (double)tl.o[0];
-    const double yl = (DIM == 3) ? Y - (double)tl.o[1] : 0.0;
-    const double zl = Z - (double)tl.o[2];
-
-    // ---- gather at x^n: node and half-node supports per direction
+    // ---- gather at x^n: node and half-node supports per direction (tile-local nodes)
     Support<ORDER, R> nd[3], hf[3];
-    supports<ORDER, R>(xl, nd[0], hf[0]);
-    supports<ORDER, R>(zl, nd[2], hf[2]);
+    supports_at<ORDER, R>(X, tl.o[0], nd[0], hf[0]);
+    supports_at<ORDER, R>(Z, tl.o[2], nd[2], hf[2]);
     if (DIM == 3) {
-        supports<ORDER, R>(yl, nd[1], hf[1]);
+        supports_at<ORDER, R>(Y, tl.o[1], nd[1], hf[1]);
     } else {
         nd[1].s = -1;
         nd[1].w[0] = A::c(1.0);
@@ -644,18 +769,9 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         }
     }
     const int SX = S.ebs[0], SY = S.ebs[1];
-    const R* Ex = sEB;
-    const R* Ey = sEB + P.eb_stride;
-    const R* Ez = sEB + 2 * P.eb_stride;
-    const R* Bx = sEB + 3 * P.eb_stride;
-    const R* By = sEB + 4 * P.eb_stride;
-    const R* Bz = sEB + 5 * P.eb_stride;
-    const R e0 = interp<R, ORDER, DIM>(Ex, SX, SY, hf[0], nd[1], nd[2]);
-    const R e1 = interp<R, ORDER, DIM>(Ey, SX, SY, nd[0], hf[1], nd[2]);
-    const R e2 = interp<R, ORDER, DIM>(Ez, SX, SY, nd[0], nd[1], hf[2]);
-    const R b0 = interp<R, ORDER, DIM>(Bx, SX, SY, nd[0], hf[1], hf[2]);
-    const R b1 = interp<R, ORDER, DIM>(By, SX, SY, hf[0], nd[1], hf[2]);
-    const R b2 = interp<R, ORDER, DIM>(Bz, SX, SY, hf[0], hf[1], nd[2]);
+    R ev[3], bv[3];
+    gather6<R, ORDER, DIM>(sEB, P.eb_stride, SX, SY, nd, hf, ev, bv);
+    const R e0 = ev[0], e1 = ev[1], e2 = ev[2], b0 = bv[0], b1 = bv[1], b2 = bv[2];
 
     // ---- relativistic Boris push
     const R one = A::c(1.0);
@@ -679,12 +795,13 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     const double dY = (DIM == 3) ? A::to(v1 * dtd[1]) : 0.0;
 
     // ---- Esirkepov deposit of J^{n+1/2} from x^n to x^{n+1}
+    const double X1 = X + dX, Z1 = Z + dZ;
+    const double Y1 = (DIM == 3) ? Y + dY : 0.0;
     Support<ORDER, R> mv[3];
-    mv[0] = support<ORDER, R>(xl + dX);
-    mv[2] = support<ORDER, R>(zl + dZ);
-    if (DIM == 3) mv[1] = support<ORDER, R>(yl + dY);
+    mv[0] = support_at<ORDER, R>(X1, tl.o[0]);
+    mv[2] = support_at<ORDER, R>(Z1, tl.o[2]);
+    if (DIM == 3) mv[1] = support_at<ORDER, R>(Y1, tl.o[1]);
     else mv[1] = nd[1];
-    const R qw = A::from(sp.q * w);
     bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
     if (same) {
         if constexpr (ORDER == 1)
@@ -695,34 +812,33 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         // the ring never holds more than 31 + 32 entries: the warp drains 32
         // whenever 32 are waiting
         const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
-        sQw[0 * WQ + slot] = xl;
-        sQw[1 * WQ + slot] = zl;
-        sQw[2 * WQ + slot] = dX;
-        sQw[3 * WQ + slot] = dZ;
-        sQw[4 * WQ + slot] = sp.q * w;
-        sQw[5 * WQ + slot] = DIM == 3 ? yl : A::to(v1);
-        if (DIM == 3) sQw[6 * WQ + slot] = dY;
+        sQw[0 * WQ + slot] = X;
+        sQw[1 * WQ + slot] = Z;
+        sQw[2 * WQ + slot] = X1;
+        sQw[3 * WQ + slot] = Z1;
+        sQw[4 * WQ + slot] = A::to(qw);
+        sQw[5 * WQ + slot] = DIM == 3 ? Y : A::to(v1);
+        if (DIM == 3) sQw[6 * WQ + slot] = Y1;
     }
 
     // ---- new position, boundary, re-sort key
-    const double nxd = (double)S.n[0], nyd = (double)S.n[1], nzd = (double)S.n[2];
-    X += dX;
-    Z += dZ;
-    if (is_neg(X)) X += nxd;
-    if (ge_pos(X, nxd)) X -= nxd;
+    X = X1;
+    Z = Z1;
+    if (is_neg(X)) X += S.nd[0];
+    if (ge_pos(X, S.nd[0])) X -= S.nd[0];
     if (DIM == 3) {
-        Y += dY;
-        if (is_neg(Y)) Y += nyd;
-        if (ge_pos(Y, nyd)) Y -= nyd;
+        Y = Y1;
+        if (is_neg(Y)) Y += S.nd[1];
+        if (ge_pos(Y, S.nd[1])) Y -= S.nd[1];
     }
-    int key;
+    int key = -1;
     if (S.absorb > 0) {
-        if (Z < (double)S.absorb || Z >= (double)(S.n[2] - S.absorb)) key = S.ntiles;
-        else key = -1;
+        // z < A or z >= n - A for integer bounds: compare floor(z)
+        const int iz = ifloor(Z);
+        if (iz < S.absorb || iz >= S.n[2] - S.absorb) key = S.ntiles;
     } else {
-        if (is_neg(Z)) Z += nzd;
-        if (ge_pos(Z, nzd)) Z -= nzd;
-        key = -1;
+        if (is_neg(Z)) Z += S.nd[2];
+        if (ge_pos(Z, S.nd[2])) Z -= S.nd[2];
     }
     if (key < 0) {
         int ix = min(max(ifloor(X), 0), S.n[0] - 1);
@@ -743,25 +859,25 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
 // A warp deposits n <= 32 queued (cell-crossing) particles of its ring,
 // starting at slot head, on the ORDER + 2 window: lane i takes entry head + i.
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain_warp(const SimDev& S, double* __restrict__ sJ,
+__device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
                                            const double* __restrict__ sQw, unsigned head, unsigned n,
                                            const SmemPlan& P, const R* jf, int32_t* err) {
     using A = Arith<R>;
     const unsigned lane = threadIdx.x & 31u;
     if (lane >= n) return;
     const unsigned i = (head + lane) & (WQ - 1);
-    const double xl = sQw[0 * WQ + i], zl = sQw[1 * WQ + i];
-    const double dX = sQw[2 * WQ + i], dZ = sQw[3 * WQ + i], qw = sQw[4 * WQ + i];
-    const double yl = DIM == 3 ? sQw[5 * WQ + i] : 0.0, vy = DIM == 3 ? 0.0 : sQw[5 * WQ + i];
-    const double dY = DIM == 3 ? sQw[6 * WQ + i] : 0.0;
+    const double X = sQw[0 * WQ + i], Z = sQw[1 * WQ + i];
+    const double X1 = sQw[2 * WQ + i], Z1 = sQw[3 * WQ + i], qw = sQw[4 * WQ + i];
+    const double Y = DIM == 3 ? sQw[5 * WQ + i] : 0.0, vy = DIM == 3 ? 0.0 : sQw[5 * WQ + i];
+    const double Y1 = DIM == 3 ? sQw[6 * WQ + i] : 0.0;
     Support<ORDER, R> nd[3], mv[3];
-    nd[0] = support<ORDER, R>(xl);
-    nd[2] = support<ORDER, R>(zl);
-    mv[0] = support<ORDER, R>(xl + dX);
-    mv[2] = support<ORDER, R>(zl + dZ);
+    nd[0] = support_at<ORDER, R>(X, tl.o[0]);
+    nd[2] = support_at<ORDER, R>(Z, tl.o[2]);
+    mv[0] = support_at<ORDER, R>(X1, tl.o[0]);
+    mv[2] = support_at<ORDER, R>(Z1, tl.o[2]);
     if (DIM == 3) {
-        nd[1] = support<ORDER, R>(yl);
-        mv[1] = support<ORDER, R>(yl + dY);
+        nd[1] = support_at<ORDER, R>(Y, tl.o[1]);
+        mv[1] = support_at<ORDER, R>(Y1, tl.o[1]);
     } else {
         nd[1].s = -1;
         nd[1].w[0] = A::c(1.0);
@@ -770,6 +886,26 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, double* __restrict__
     if (!deposit<R, DIM, ORDER, ORDER + 2>(S, sJ, P, A::from(qw), A::from(vy), jf, nd[0], nd[1], nd[2],
                                            mv[0], mv[1], mv[2]))
         atomicOr(err, PIC_DERR_BOUNDS);
+}
+
+// float-float keeps the drain out of line: the cell-crossing deposit is long
+// and rare, and inlined into the particle loop it crowds the instruction cache
+// (about 5 % of the kernel); FP64 is indifferent and inlines it
+template <class R, int DIM, int ORDER>
+__device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
+                                                 const double* __restrict__ sQw, unsigned head, unsigned n,
+                                                 const SmemPlan& P, const R* jf, int32_t* err) {
+    drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
+}
+
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
+                                      const double* __restrict__ sQw, unsigned head, unsigned n,
+                                      const SmemPlan& P, const R* jf, int32_t* err) {
+    if constexpr (std::is_same<R, double>::value)
+        drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
+    else
+        drain_warp_outlined<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -845,6 +981,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         for (int spi = 0; spi < S.nsp; ++spi) {
             const SpeciesDev& sp = S.sp[spi];
             const R kq = A::from(sp.kq);
+            const R qs = A::from(sp.q);
             const int t_first = unit.box * S.tiles_per_box;
             const int t_end = t_first + S.tiles_per_box;
             const int64_t b0 = sp.off[t_first], nbp = sp.off[t_end] - b0;
@@ -908,12 +1045,12 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
                         const int64_t p = p0 + lane;
                         if (p < s1)
-                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, sJ, sQw, s_qtail + warp, P, jf, dtd, kq, p,
+                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, sJ, sQw, s_qtail + warp, P, jf, dtd, kq, qs, p,
                                                     sd->err);
                         __syncwarp();
                         const unsigned head = s_qhead[warp], tail = *vtail;
                         if (tail - head >= 32u) {
-                            drain_warp<R, DIM, ORDER>(S, sJ, sQw, head, 32u, P, jf, sd->err);
+                            drain<R, DIM, ORDER>(S, cur, sJ, sQw, head, 32u, P, jf, sd->err);
                             __syncwarp();
                             if (lane == 0) s_qhead[warp] = head + 32u;
                             __syncwarp();
@@ -922,7 +1059,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     __syncwarp();
                     const unsigned head = s_qhead[warp], tail = *vtail;
                     if (tail != head) {
-                        drain_warp<R, DIM, ORDER>(S, sJ, sQw, head, tail - head, P, jf, sd->err);
+                        drain<R, DIM, ORDER>(S, cur, sJ, sQw, head, tail - head, P, jf, sd->err);
                         __syncwarp();
                         if (lane == 0) s_qhead[warp] = tail;
                     }

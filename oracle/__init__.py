@@ -63,6 +63,7 @@ def lib():
             L.orc_add_species.argtypes = [ctypes.c_void_p, _d, _d, _i64] + [_pd] * 7 + [_pi64]
             L.orc_set_laser.argtypes = [ctypes.c_void_p] + [_d] * 7 + [_i64]
             L.orc_set_field.argtypes = [ctypes.c_void_p, ctypes.c_int, _pd]
+            L.orc_set_gather.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, _pd]
             L.orc_num_particles.restype = _i64
             L.orc_num_particles.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -140,6 +141,11 @@ class OracleSim:
     def set_laser(self, a0, w0, tau, t_peak, omega, xc, yc, k_ant):
         if lib().orc_set_laser(self._h, a0, w0, tau, t_peak, omega, xc, yc, int(k_ant)) != 0:
             raise ValueError("oracle rejected the laser")
+
+    def set_gather(self, energy_conserving: bool):
+        """Field gather: energy-conserving (order - 1 along staggered directions) or not."""
+        if lib().orc_set_gather(self._h, int(bool(energy_conserving))) != 0:
+            raise ValueError("bad gather kind")
 
     def set_field(self, comp, data):
         a = _c64(data).reshape(-1)

@@ -13,8 +13,12 @@
  *   - field update: B half step, E full step with J, B half step.
  *   - relativistic Boris push (Boris 1970).
  *   - Esirkepov charge-conserving deposit (Esirkepov, CPC 135 (2001) 144).
- *   - B-spline shapes of order 1 or 2, every component interpolated at its
- *     own staggered location with the same order in every direction.
+ *   - B-spline shapes of order 1, 2 or 3, every component interpolated at
+ *     its own staggered location.  Default ("momentum-conserving" style): the
+ *     run's order in every direction.  Energy-conserving variant (the
+ *     Galerkin gather of Yee-grid PIC codes): one order lower along each
+ *     direction in which the component is staggered, which makes the gather
+ *     the transpose of the Esirkepov deposit (checked in the pins).
  * Parity with the CUDA path is checked on these definitions; the physics
  * pins (dispersion, gyration, plasma frequency, continuity, Gauss) are in the
  * tests.
@@ -39,6 +43,7 @@ struct orc_sim {
     double d[3];
     double dt;
     int order;
+    int ec;     /* 1: energy-conserving gather (order - 1 along staggered directions) */
     int absorb;
     int64_t step;
     double* f[9]; /* Ex Ey Ez Bx By Bz Jx Jy Jz */
@@ -67,10 +72,12 @@ static int64_t idx3(const orc_sim* s, int64_t i, int64_t j, int64_t k) {
     return (wrap(k, s->n[2]) * s->n[1] + wrap(j, s->n[1])) * s->n[0] + wrap(i, s->n[0]);
 }
 
-/* B-spline shape S(dist): order 1 is the hat 1-|d| on |d|<1; order 2 is
+/* B-spline shape S(dist): order 0 is the box, 1 on -1/2 <= d < 1/2 (half
+ * open, so that exactly one node carries a point); order 1 is the hat 1-|d| on |d|<1; order 2 is
  * 3/4-d^2 on |d|<1/2 and (3/2-|d|)^2/2 on 1/2<=|d|<3/2; order 3 (the paper's
  * choice, Sec. 3.1) is 2/3-d^2+|d|^3/2 on |d|<1 and (2-|d|)^3/6 on 1<=|d|<2. */
 double orc_shape(int order, double dist) {
+    if (order == 0) return (dist >= -0.5 && dist < 0.5) ? 1.0 : 0.0;
     double a = fabs(dist);
     if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
     if (order == 2) {
@@ -86,6 +93,7 @@ double orc_shape(int order, double dist) {
 /* first node of the (order+1)-point support of S around the point xi
  * (xi in cell units, measured from the component's own grid origin). */
 static int64_t support_start(int order, double xi) {
+    if (order == 0) return (int64_t)floor(xi + 0.5);
     if (order == 1) return (int64_t)floor(xi);
     if (order == 2) return (int64_t)floor(xi + 0.5) - 1;
     return (int64_t)floor(xi) - 1;
@@ -187,27 +195,35 @@ int orc_get_particles(const orc_sim* s, int species, double* x, double* y, doubl
 
 /* ------------------------------------------------------------------ */
 /* Field gather: each component interpolated at its own staggered grid  */
-/* with S of the run's order in every (active) direction.               */
+/* with S of the run's order in every (active) direction, or, for the   */
+/* energy-conserving variant, of order - 1 along the directions in      */
+/* which the component sits at half nodes.                              */
 /* ------------------------------------------------------------------ */
 static double gather_comp(const orc_sim* s, int comp, const double X[3]) {
-    int o = s->order;
-    int np1 = o + 1;
     int64_t base[3];
+    int npts[3];
     double wt[3][4];
     for (int a = 0; a < 3; a++) {
-        if (a == 1 && s->dim == 2) { base[a] = 0; wt[a][0] = 1.0; continue; }
+        if (a == 1 && s->dim == 2) { base[a] = 0; npts[a] = 1; wt[a][0] = 1.0; continue; }
+        int o = (s->ec && STAG[comp][a] == 0.5) ? s->order - 1 : s->order;
         double xi = X[a] - STAG[comp][a];
         base[a] = support_start(o, xi);
-        for (int l = 0; l < np1; l++) wt[a][l] = orc_shape(o, xi - (double)(base[a] + l));
+        npts[a] = o + 1;
+        for (int l = 0; l < npts[a]; l++) wt[a][l] = orc_shape(o, xi - (double)(base[a] + l));
     }
-    int ny_pts = (s->dim == 2) ? 1 : np1;
     double sum = 0.0;
-    for (int c = 0; c < np1; c++)
-        for (int b = 0; b < ny_pts; b++)
-            for (int a = 0; a < np1; a++)
+    for (int c = 0; c < npts[2]; c++)
+        for (int b = 0; b < npts[1]; b++)
+            for (int a = 0; a < npts[0]; a++)
                 sum += wt[0][a] * wt[1][b] * wt[2][c] *
                        s->f[comp][idx3(s, base[0] + a, base[1] + b, base[2] + c)];
     return sum;
+}
+
+int orc_set_gather(orc_sim* s, int energy_conserving) {
+    if (!s || (energy_conserving != 0 && energy_conserving != 1)) return -1;
+    s->ec = energy_conserving;
+    return 0;
 }
 
 int orc_gather(const orc_sim* s, double x, double y, double z, double eb_out[6]) {
@@ -582,7 +598,7 @@ int orc_bin_particles(int dim, const int64_t n[3], const double d[3], const int6
     }
     for (int64_t b = 0; b < nboxes; b++) box_off[b + 1] += box_off[b];
     /* stable placement: particles visited in ascending index */
-    int64_t* fill = (int64_t*)calloc((size_t)nboxes, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)(nboxes > 0 ? nboxes : 1), sizeof(int64_t));
     for (int64_t p = 0; p < np; p++) perm[box_off[box[p]] + fill[box[p]]++] = p;
     free(fill);
     free(box);

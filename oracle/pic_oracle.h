@@ -54,6 +54,12 @@ int orc_add_species(orc_sim* s, double q, double m, int64_t np,
 int orc_set_laser(orc_sim* s, double a0, double w0, double tau, double t_peak,
                   double omega, double xc, double yc, int64_t k_ant);
 
+/* field gather: 0 = the run's order in every direction (default); 1 =
+ * energy-conserving: order - 1 along each direction in which the component
+ * is staggered (Ex along x, Bx along y and z, ...), order-0 being the box
+ * shape on the nearest half node. */
+int orc_set_gather(orc_sim* s, int energy_conserving);
+
 int orc_set_field(orc_sim* s, int comp, const double* data);
 int orc_get_field(const orc_sim* s, int comp, double* out);
 int64_t orc_num_particles(const orc_sim* s, int species);
@@ -80,7 +86,7 @@ int orc_bin_particles(int dim, const int64_t n[3], const double d[3], const int6
                       int64_t* box_off_out, int64_t* perm_out);
 
 /* ---- pieces exposed for the pin tests ---- */
-double orc_shape(int order, double dist);     /* B-spline S(dist) */
+double orc_shape(int order, double dist);     /* B-spline S(dist), order 0..3 */
 /* single-particle gather of all six E/B components at (x,y,z) */
 int orc_gather(const orc_sim* s, double x, double y, double z, double eb_out[6]);
 /* one Boris push of u given E, B; returns u in place */

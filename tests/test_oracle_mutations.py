@@ -69,6 +69,12 @@ MUTATIONS = [
     ("particles: upper absorbing boundary ignored", "if (np_[2] < zlo || np_[2] >= zhi) drop[ndrop++] = p;",
      "if (np_[2] < zlo) drop[ndrop++] = p;"),
     ("speedup model: exponent dropped", "return pow(1.0 / e0, x);", "return 1.0 / e0;"),
+    ("energy-conserving gather: lower order along node directions",
+     "int o = (s->ec && STAG[comp][a] == 0.5) ? s->order - 1 : s->order;",
+     "int o = (s->ec && STAG[comp][a] == 0.0) ? s->order - 1 : s->order;"),
+    ("energy-conserving gather: box shape from floor instead of the nearest node",
+     "if (order == 0) return (int64_t)floor(xi + 0.5);", "if (order == 0) return (int64_t)floor(xi);"),
+    ("energy-conserving gather: flag ignored", "    s->ec = energy_conserving;\n", "    s->ec = 0;\n"),
 ]
 
 

@@ -524,3 +524,107 @@ def test_bin_particles_by_hand():
     # boxes: p0 0, p1 3, p2 2, p3 1, p4 2, p5 1, p6 2
     assert list(off) == [0, 1, 3, 6, 7]
     assert list(perm) == [0, 3, 5, 2, 4, 6, 1]
+
+
+# ------------------------------------------- energy-conserving gather ---
+def _gl3_on(f, a, b):
+    """3-point Gauss-Legendre on [a, b] (interior nodes only, so a jump at
+    an end does not matter): exact for polynomials of degree <= 5."""
+    return (b - a) * _gl3(lambda s: f(a + s * (b - a)))
+
+
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (3, 3), (2, 1), (2, 2), (2, 3)])
+def test_energy_conserving_gather_is_the_transpose_of_esirkepov(dim, order):
+    """For a straight move along one axis a, the Esirkepov current J_a is
+    the path integral of the order-(n-1) shape on the half-node grid times the
+    order-n transverse shapes (the B-spline derivative identity), so for any
+    grid field G on the J_a locations
+        sum_cells J_a G dV dt = q w * integral over the path of G gathered with
+        order n - 1 along a and order n across it,
+    which is the energy-conserving gather of E_a.  The gather is piecewise
+    polynomial of degree <= 3 between multiples of half a cell, so Gauss-
+    Legendre quadrature on those pieces is exact.  The default gather (order n along a)
+    misses the identity, which the last check shows."""
+    n = (10, 10 if dim == 3 else 1, 10)
+    d = (0.5, 0.6 if dim == 3 else 1.0, 0.7)
+    dt = 0.99 / math.sqrt(sum(1 / x ** 2 for x in (d if dim == 3 else (d[0], d[2]))))
+    rng = np.random.default_rng(70 + 10 * dim + order)
+    axes = (0, 1, 2) if dim == 3 else (0, 2)
+    for a in axes:
+        for trial in range(4):
+            X0 = rng.uniform(4.0, 6.0, 3)
+            if dim == 2:
+                X0[1] = 0.0
+            u = np.zeros(3)
+            u[a] = rng.choice([-1.0, 1.0]) * rng.uniform(0.5, 6.0)
+            q, w = rng.choice([-1.0, 1.0]), rng.uniform(0.3, 2.0)
+            pos = X0 * np.array(d)
+            sim = orc.OracleSim(dim, n, d, dt, order)
+            sim.add_species(q, 1.0, [pos[0]], [pos[1]], [pos[2]], [u[0]], [u[1]], [u[2]], [w])
+            sim.step(1)  # zero fields: the push leaves u unchanged
+            J = sim.field(orc.JX + a)
+            G = rng.normal(size=J.shape)
+            lhs = float((J * G).sum()) * d[0] * d[1] * d[2] * dt
+            X1 = X0.copy()
+            X1[a] = sim.particles(0)[("x", "y", "z")[a]][0] / d[a]
+            rhs = {}
+            for ec in (True, False):
+                probe = orc.OracleSim(dim, n, d, dt, order)
+                probe.set_gather(ec)
+                probe.set_field(orc.EX + a, G)
+
+                def field_at(t):
+                    P = X0.copy()
+                    P[a] = t
+                    return probe.gather(*(P * np.array(d)))[a]
+
+                lo, hi = sorted((X0[a], X1[a]))
+                cuts = [lo] + [k / 2 for k in range(math.floor(2 * lo) + 1, math.ceil(2 * hi))] + [hi]
+                integ = sum(_gl3_on(field_at, cuts[m], cuts[m + 1]) for m in range(len(cuts) - 1))
+                rhs[ec] = q * w * d[a] * integ * (1.0 if X1[a] >= X0[a] else -1.0)
+            assert abs(lhs - rhs[True]) <= 1e-12 * max(abs(lhs), 1e-300), (a, trial, lhs, rhs[True])
+            assert abs(lhs - rhs[False]) > 1e-6 * abs(lhs), (a, trial)
+
+
+# variance of the centred B-spline of order m (m + 1 unit boxes convolved)
+_BSPLINE_VAR = {1: 1 / 6, 2: 1 / 4, 3: 1 / 3}
+
+
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 2), (3, 3), (2, 2)])
+def test_energy_conserving_gather_orders_per_direction(dim, order):
+    """A field equal to the square of a grid coordinate, h^2, gathered with a
+    centred B-spline of order m >= 2 gives x^2 + (m + 1)/12 (splines of degree
+    >= 2 reproduce quadratics; the constant is the spline's variance), with
+    the hat (m = 1) x^2 + t (1 - t), t the fraction of x on that grid.  So each component shows,
+    direction by direction, which order it was gathered with: order - 1 along
+    the directions where it sits at half nodes (Ex along x; Bx along y and z;
+    ...), order n elsewhere; order 0 picks the nearest half node."""
+    n = (14, 14 if dim == 3 else 1, 14)
+    d = (1.0, 1.0, 1.0)
+    sim = orc.OracleSim(dim, n, d, 0.1, order)
+    sim.set_gather(True)
+    rng = np.random.default_rng(90 + order)
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    idx = (i, j, k)
+    axes = (0, 1, 2) if dim == 3 else (0, 2)
+    for a in axes:
+        for c in range(6):
+            h = idx[a] + STAG[c][a]
+            for comp in range(6):
+                sim.set_field(comp, np.zeros(i.shape))
+            sim.set_field(c, h.astype(np.float64) ** 2)
+            for _ in range(12):
+                P = rng.uniform(5.0, 9.0, 3)
+                if dim == 2:
+                    P[1] = 0.0
+                got = sim.gather(*P)[c]
+                m = order - 1 if STAG[c][a] == 0.5 else order
+                x = P[a]
+                if m == 0:  # nearest half node
+                    want = (math.floor(x) + 0.5) ** 2
+                elif m == 1:  # linear interpolation of h^2: x^2 + t (1 - t)
+                    t = (x - STAG[c][a]) - math.floor(x - STAG[c][a])
+                    want = x * x + t * (1.0 - t)
+                else:
+                    want = x * x + _BSPLINE_VAR[m]
+                assert abs(got - want) < 1e-12, (a, c, order, got, want)

@@ -119,6 +119,18 @@ pic_status pic_add_laser(pic_sim* sim, const pic_laser_desc* laser);
  * the layout given at the top of this file (host or device pointer). */
 pic_status pic_set_field(pic_sim* sim, int comp, const double* data, int on_device);
 
+/* Field gather kind.  PIC_GATHER_MOMENTUM (default): every component
+ * interpolated at its own staggered location with the run's shape order in
+ * every direction.  PIC_GATHER_ENERGY: the energy-conserving (Galerkin)
+ * gather, one order lower along each direction in which the component sits
+ * at half nodes (Ex along x, Bx along y and z, ...; order 0 is the nearest
+ * half node), which makes the gather the transpose of the Esirkepov deposit.
+ * The paper runs WarpX (Sec. 3), whose Yee-grid runs offer both; it does not
+ * say which it used.  May be called at any time; takes effect from the next
+ * step.  Synchronises the stream.  Errors: PIC_EINVAL (unknown kind). */
+enum { PIC_GATHER_MOMENTUM = 0, PIC_GATHER_ENERGY = 1 };
+pic_status pic_set_gather(pic_sim* sim, int kind);
+
 /* ---- load balancing (Sec. 2.2) ------------------------------------------- */
 enum { PIC_POLICY_KNAPSACK = 0, PIC_POLICY_SFC = 1 };
 enum { PIC_COST_HEURISTIC = 0, PIC_COST_DEVICE_CLOCK = 1, PIC_COST_KERNEL_TIME = 2 };

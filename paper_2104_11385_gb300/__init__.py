@@ -3,7 +3,8 @@ load balancing (after arXiv 2104.11385).  The compute path is libpic.so
 (hand-written CUDA for sm_103a behind the C ABI in include/pic_api.h); this
 package is the thin Python binding over it."""
 from . import _lib
-from ._lib import (BX, BY, BZ, COST_DEVICE_CLOCK, COST_HEURISTIC, COST_KERNEL_TIME, EX, EY, EZ, JX, JY, JZ, LB_DYNAMIC,
+from ._lib import (BX, BY, BZ, COST_DEVICE_CLOCK, COST_HEURISTIC, COST_KERNEL_TIME, EX, EY, EZ, GATHER_ENERGY,
+                   GATHER_MOMENTUM, JX, JY, JZ, LB_DYNAMIC,
                    LB_NONE, LB_STATIC, POLICY_KNAPSACK, POLICY_SFC, RHO, SCHED_LISTS, SCHED_QUEUE,
                    PicError)
 from .sim import Simulation, balance_compute, lb_efficiency, lb_params
@@ -26,6 +27,8 @@ def from_workload(wl: dict, stream=None, species_on_device=False) -> Simulation:
         sim.add_laser(L["a0"], L["w0"], L["tau"], L["t_peak"], L["omega"], L["xc"], L["yc"], L["k_ant"])
     if wl.get("rho0"):
         sim.add_background(wl["rho0"])
+    if wl.get("gather") == "energy":
+        sim.set_gather(True)
     return sim
 
 

@@ -57,6 +57,7 @@ class LaunchCfg(ctypes.Structure):
 
 
 PREC_FP64, PREC_FLOAT_FLOAT = 1, 2
+GATHER_MOMENTUM, GATHER_ENERGY = 0, 1
 
 
 class Stats(ctypes.Structure):
@@ -97,6 +98,7 @@ SIGNATURES = [
     ("pic_add_background", _int, [_vp, _d]),
     ("pic_add_laser", _int, [_vp, ctypes.POINTER(LaserDesc)]),
     ("pic_set_field", _int, [_vp, _int, _vp, _int]),
+    ("pic_set_gather", _int, [_vp, _int]),
     ("pic_set_lb_params", _int, [_vp, ctypes.POINTER(LBParams)]),
     ("pic_step", _int, [_vp, _int]),
     ("pic_sync", _int, [_vp]),

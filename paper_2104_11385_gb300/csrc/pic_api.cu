@@ -836,6 +836,19 @@ pic_status pic_set_field(pic_sim* s, int comp, const double* data, int on_device
     return PIC_OK;
 }
 
+pic_status pic_set_gather(pic_sim* s, int kind) {
+    TRY(check(s));
+    if (kind != PIC_GATHER_MOMENTUM && kind != PIC_GATHER_ENERGY)
+        return fail(s, PIC_EINVAL, "unknown gather kind %d", kind);
+    // after the first step the device copy owns the species buffer pointers
+    if (s->stepped) {
+        TRY(sync_and_check(s));
+        TRY(pull_sim(s));
+    }
+    s->h.ec = kind == PIC_GATHER_ENERGY ? 1 : 0;
+    return upload_sim(s);
+}
+
 pic_status pic_set_lb_params(pic_sim* s, const pic_lb_params* p) {
     TRY(check(s));
     TRY(validate_lb(s, p));

@@ -58,6 +58,7 @@ struct LaserDev {
 struct SimDev {
     CUtensorMap tmap[6];  // TMA descriptors of the padded E,B arrays (must stay first)
     int dim, order, nsp, absorb;
+    int ec;               // 1: energy-conserving gather (order - 1 along staggered directions)
     int n[3];             // cells per direction
     int pn[3];            // padded extents (n + 2G; 1 for an inactive y)
     int g[3];             // guard width per direction (G or 0)

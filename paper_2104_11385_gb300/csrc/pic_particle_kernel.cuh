@@ -182,22 +182,33 @@ __device__ __forceinline__ Support<ORDER, R> support(double xi) {
 }
 
 // node and half-node supports of one position (the half-node grid is shifted
-// by +1/2 cell: Ex along x, etc.)
+// by +1/2 cell: Ex along x, etc.), and the cell floor(xi).  ec selects the
+// energy-conserving half-node support: order ORDER - 1 (order 0: the nearest
+// half node), stored with a zero last weight so that the interpolation code
+// is shared.
 template <int ORDER, class R>
-__device__ __forceinline__ void supports(double xi, Support<ORDER, R>& nd, Support<ORDER, R>& hf) {
+__device__ __forceinline__ void supports(double xi, bool ec, Support<ORDER, R>& nd, Support<ORDER, R>& hf,
+                                         int& cell) {
     using A = Arith<R>;
     double f;
     const int i = ifloor_frac(xi, f);
+    cell = i;
     const bool up = ge_half(f);
     const R fr = A::from(f);
     if constexpr (ORDER == 1) {
         nd.s = i;
         nd.w[0] = A::c(1.0) - fr;
         nd.w[1] = fr;
-        const R g = fr + (up ? A::c(-0.5) : A::c(0.5));  // xi - 1/2 - floor(xi - 1/2)
-        hf.s = up ? i : i - 1;
-        hf.w[0] = A::c(1.0) - g;
-        hf.w[1] = g;
+        if (ec) {  // box shape: half node i (at i + 1/2) carries the point
+            hf.s = i;
+            hf.w[0] = A::c(1.0);
+            hf.w[1] = A::c(0.0);
+        } else {
+            const R g = fr + (up ? A::c(-0.5) : A::c(0.5));  // xi - 1/2 - floor(xi - 1/2)
+            hf.s = up ? i : i - 1;
+            hf.w[0] = A::c(1.0) - g;
+            hf.w[1] = g;
+        }
     } else if constexpr (ORDER == 2) {
         const R d = up ? fr - A::c(1.0) : fr;  // node: xi - floor(xi + 1/2)
         const R a = A::c(0.5) - d, b = A::c(0.5) + d;
@@ -205,18 +216,36 @@ __device__ __forceinline__ void supports(double xi, Support<ORDER, R>& nd, Suppo
         nd.w[0] = A::c(0.5) * (a * a);
         nd.w[1] = fma(-d, d, A::c(0.75));
         nd.w[2] = A::c(0.5) * (b * b);
-        const R h = fr - A::c(0.5);  // half: (xi - 1/2) - floor(xi), nearest half-node floor(xi)
-        const R ah = A::c(0.5) - h, bh = A::c(0.5) + h;
-        hf.s = i - 1;
-        hf.w[0] = A::c(0.5) * (ah * ah);
-        hf.w[1] = fma(-h, h, A::c(0.75));
-        hf.w[2] = A::c(0.5) * (bh * bh);
+        if (ec) {  // hat on the half-node grid: g = frac(xi - 1/2)
+            const R g = fr + (up ? A::c(-0.5) : A::c(0.5));
+            hf.s = up ? i : i - 1;
+            hf.w[0] = A::c(1.0) - g;
+            hf.w[1] = g;
+            hf.w[2] = A::c(0.0);
+        } else {
+            const R h = fr - A::c(0.5);  // half: (xi - 1/2) - floor(xi), nearest half-node floor(xi)
+            const R ah = A::c(0.5) - h, bh = A::c(0.5) + h;
+            hf.s = i - 1;
+            hf.w[0] = A::c(0.5) * (ah * ah);
+            hf.w[1] = fma(-h, h, A::c(0.75));
+            hf.w[2] = A::c(0.5) * (bh * bh);
+        }
     } else {
         nd.s = i - 1;
         cubic_weights<R>(fr, nd.w);
-        const R g = fr + (up ? A::c(-0.5) : A::c(0.5));
-        hf.s = (up ? i : i - 1) - 1;
-        cubic_weights<R>(g, hf.w);
+        if (ec) {  // quadratic on the half-node grid around the nearest half node floor(xi)
+            const R h = fr - A::c(0.5);
+            const R ah = A::c(0.5) - h, bh = A::c(0.5) + h;
+            hf.s = i - 1;
+            hf.w[0] = A::c(0.5) * (ah * ah);
+            hf.w[1] = fma(-h, h, A::c(0.75));
+            hf.w[2] = A::c(0.5) * (bh * bh);
+            hf.w[3] = A::c(0.0);
+        } else {
+            const R g = fr + (up ? A::c(-0.5) : A::c(0.5));
+            hf.s = (up ? i : i - 1) - 1;
+            cubic_weights<R>(g, hf.w);
+        }
     }
 }
 
@@ -229,10 +258,12 @@ __device__ __forceinline__ Support<ORDER, R> support_at(double x, int o) {
     return r;
 }
 template <int ORDER, class R>
-__device__ __forceinline__ void supports_at(double x, int o, Support<ORDER, R>& nd, Support<ORDER, R>& hf) {
-    supports<ORDER, R>(x, nd, hf);
+__device__ __forceinline__ void supports_at(double x, int o, bool ec, Support<ORDER, R>& nd,
+                                            Support<ORDER, R>& hf, int& cell) {
+    supports<ORDER, R>(x, ec, nd, hf, cell);
     nd.s -= o;
     hf.s -= o;
+    cell -= o;
 }
 
 // E/B tile halo below the tile origin: 1 cell (orders 1, 2), 2 cells (order 3)
@@ -739,28 +770,22 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
 
     // ---- gather at x^n: node and half-node supports per direction (tile-local nodes)
     Support<ORDER, R> nd[3], hf[3];
-    supports_at<ORDER, R>(X, tl.o[0], nd[0], hf[0]);
-    supports_at<ORDER, R>(Z, tl.o[2], nd[2], hf[2]);
+    int cx, cy = 0, cz;
+    const bool ec = S.ec != 0;
+    supports_at<ORDER, R>(X, tl.o[0], ec, nd[0], hf[0], cx);
+    supports_at<ORDER, R>(Z, tl.o[2], ec, nd[2], hf[2], cz);
     if (DIM == 3) {
-        supports_at<ORDER, R>(Y, tl.o[1], nd[1], hf[1]);
+        supports_at<ORDER, R>(Y, tl.o[1], ec, nd[1], hf[1], cy);
     } else {
         nd[1].s = -1;
         nd[1].w[0] = A::c(1.0);
         hf[1] = nd[1];
     }
     {
-        // the particle must sit in its tile (local cell index in [0, T))
-        bool in;
-        if (ORDER == 1) {  // node support start = floor(xl)
-            in = nd[0].s >= 0 && nd[0].s < S.T[0] && nd[2].s >= 0 && nd[2].s < S.T[2];
-            if (DIM == 3) in = in && nd[1].s >= 0 && nd[1].s < S.T[1];
-        } else if (ORDER == 3) {  // node support start = floor(xl) - 1
-            in = nd[0].s >= -1 && nd[0].s < S.T[0] - 1 && nd[2].s >= -1 && nd[2].s < S.T[2] - 1;
-            if (DIM == 3) in = in && nd[1].s >= -1 && nd[1].s < S.T[1] - 1;
-        } else {  // quadratic: half-node support start = floor(xl) - 1
-            in = hf[0].s >= -1 && hf[0].s < S.T[0] - 1 && hf[2].s >= -1 && hf[2].s < S.T[2] - 1;
-            if (DIM == 3) in = in && hf[1].s >= -1 && hf[1].s < S.T[1] - 1;
-        }
+        // the particle must sit in its tile (local cell index in [0, T)); the
+        // E/B halo then covers every support above
+        bool in = cx >= 0 && cx < S.T[0] && cz >= 0 && cz < S.T[2];
+        if (DIM == 3) in = in && cy >= 0 && cy < S.T[1];
         if (!in) {
             atomicOr(err, PIC_DERR_BOUNDS);
             sp.key[p] = S.ntiles;

@@ -118,6 +118,11 @@ class Simulation:
         p, dev, k = _ptr(data if type(data).__module__.startswith("torch") else np.asarray(data, np.float64))
         self._check(self._lib.pic_set_field(self._h, int(comp), p, dev))
 
+    def set_gather(self, energy_conserving: bool):
+        """Energy-conserving (order - 1 along staggered directions) or default field gather."""
+        kind = L.GATHER_ENERGY if energy_conserving else L.GATHER_MOMENTUM
+        self._check(self._lib.pic_set_gather(self._h, kind))
+
     def set_lb_params(self, **kw):
         self._check(self._lib.pic_set_lb_params(self._h, ctypes.byref(lb_params(**kw))))
 

@@ -122,6 +122,7 @@ def test_bad_arguments_are_status_codes():
     assert lib.pic_init(None, ctypes.byref(h)) == L.PIC_EINVAL
     # destroying a null handle is a no-op
     assert lib.pic_destroy(None) == L.PIC_OK
+    assert lib.pic_set_gather(None, 1) == L.PIC_EINVAL
 
 
 def test_grid_validation_without_gpu():

@@ -27,6 +27,8 @@ def make_oracle(wl, fields=None):
     if fields is not None:
         for c, f in enumerate(fields):
             ref.set_field(c, f)
+    if wl.get("gather") == "energy":
+        ref.set_gather(True)
     return ref
 
 
@@ -288,3 +290,50 @@ def test_float_float_variant_uniform32_and_laser():
     sim.step(12)
     ref.step(12)
     compare(sim, ref, wl)
+
+
+EC_CASES = [
+    (3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1),
+    (3, (24, 16, 16), (8, 8, 16), (0.3, 0.35, 0.4), 2),
+    (3, (16, 16, 24), (8, 8, 8), (0.3, 0.3, 0.35), 3),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.35), 1),
+    (2, (32, 1, 64), (32, 1, 32), (0.3, 1.0, 0.3), 2),
+    (2, (48, 1, 32), (16, 1, 16), (0.3, 1.0, 0.3), 3),
+]
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp64", "float_float"])
+@pytest.mark.parametrize("case", EC_CASES, ids=[f"{c[0]}d_o{c[4]}" for c in EC_CASES])
+def test_energy_conserving_gather_parity(case, precision):
+    """Energy-conserving gather (order - 1 along each component's staggered
+    directions) against the oracle's, in both arithmetic variants; the oracle
+    pins tie this gather to the Esirkepov deposit."""
+    dim, n, box, dx, order = case
+    wl = workloads.random_plasma(900 + sum(n) + order, dim, n, box, dx, order, nspecies=2, npart=4000,
+                                 umax=2.0)
+    wl["gather"] = "energy"
+    fields = workloads.random_fields(9, n, amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    if precision == 2:
+        sim.set_launch(precision=2)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl)
+
+
+def test_gather_kind_switch_between_steps():
+    """The gather kind may change between steps (the device copy of the
+    simulation is refreshed, not the particle buffers)."""
+    wl = workloads.random_plasma(321, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=2, npart=3000,
+                                 umax=1.0)
+    fields = workloads.random_fields(10, (16, 16, 16), amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    sim.step(4)
+    ref.step(4)
+    sim.set_gather(True)
+    ref.set_gather(True)
+    sim.step(4)
+    ref.step(4)
+    compare(sim, ref, wl)
+    with pytest.raises(pic.PicError):
+        sim._check(sim._lib.pic_set_gather(sim._h, 7))

@@ -80,7 +80,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="foil256",
                     choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d"])
@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--server-requests", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--timeline", type=int, default=0,
+                    help="instead of the bench line: N steps of the workload under each load-balancing mode "
+                         "(none / static / dynamic), with E and the time per step every interval")
     return ap.parse_args()
 
 
@@ -536,6 +539,59 @@ def oracle_rate(wl_name, budget_s=15.0, steps=1):
     return nparts * done / secs, sample % (nparts, done), secs
 
 
+def run_timeline(args):
+    """The paper's comparison of load-balancing modes over a run (Sec. 3.2):
+    the same workload, launch and schedule under no balancing (the fixed
+    equal-count Morton mapping), static balancing (once, at the first
+    interval) and dynamic balancing (every interval, threshold theta), with
+    the time per step and E (Eq. 1) of the mapping in force every interval."""
+    import torch
+    import paper_2104_11385_gb300 as pic
+    wl = make_workload(args.workload, args.scale)
+    interval = int(wl.get("lb_interval", 10))
+    nint = max(1, args.timeline // interval)
+    sched = pic.SCHED_LISTS if args.sched == "lists" else pic.SCHED_QUEUE
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, mode in (("none", pic.LB_NONE), ("static", pic.LB_STATIC), ("dynamic", pic.LB_DYNAMIC)):
+        sim = pic.from_workload(wl, stream=stream.cuda_stream)
+        sim.set_lb_params(mode=mode, interval=interval, theta=0.10, policy=pic.POLICY_KNAPSACK,
+                          cost=pic.COST_DEVICE_CLOCK, split=args.split, sched=sched)
+        sim.set_launch(threads=args.threads or 256, ctas_per_sm=args.ctas_per_sm or 2,
+                       precision=args.precision)
+        ms, eff = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(nint):
+            nlog = len(sim.lb_log())
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(interval)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / interval)
+            log = sim.lb_log()[nlog:]
+            # E of the mapping used during this interval: the load-balancing
+            # call at its end measured it (e_old); otherwise read it and start
+            # a new cost window
+            eff.append(log[-1]["e_old"] if log else sim.efficiency(reset_window=True))
+        lbl = sim.lb_log()
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        out[name] = {"total_ms": sum(ms) * interval, "ms_per_step": ms, "E": eff,
+                     "mean_E": sum(eff) / len(eff),
+                     "adopted": sum(1 for r in lbl if r["adopted"]), "lb_calls": len(lbl)}
+    line = {"metric": "lb_timeline", "workload": workload_desc(wl), "steps_per_mode": nint * interval,
+            "interval": interval, "sched": args.sched, "theta": 0.10,
+            "launch": {"threads": args.threads or 256, "ctas_per_sm": args.ctas_per_sm or 2,
+                       "precision": args.precision},
+            "speedup_static_over_none": out["none"]["total_ms"] / out["static"]["total_ms"],
+            "speedup_dynamic_over_none": out["none"]["total_ms"] / out["dynamic"]["total_ms"],
+            "speedup_dynamic_over_static": out["static"]["total_ms"] / out["dynamic"]["total_ms"],
+            "modes": out}
+    print(json.dumps(line, default=_jsonable), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -565,6 +621,10 @@ def main():
         print(json.dumps(line), flush=True)
         return
 
+    if args.timeline > 0:
+        if rank == 0:
+            run_timeline(args)
+        return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")

@@ -211,6 +211,16 @@ pic_status pic_get_box_costs(pic_sim* sim, int strategy, double* costs_out, int6
 pic_status pic_rebalance(pic_sim* sim, const pic_lb_params* params, pic_lb_result* out,
                          int32_t* assign_out);
 
+/* E (Eq. 1, c_avg / c_max over workers) of the work-unit mapping in force,
+ * with the per-box costs of the current cost window (strategy as in
+ * pic_get_box_costs; a box's cost is divided evenly over its work units), as
+ * Listing 1 evaluates the current distribution before it proposes a new one.
+ * The cost window is the one pic_rebalance reads: it holds everything since
+ * the last load-balancing call.  reset_window != 0 starts a new window after
+ * the read (the next internal load-balancing call then sees only the steps
+ * after it).  Synchronises.  Errors: PIC_EINVAL. */
+pic_status pic_get_efficiency(pic_sim* sim, int strategy, int reset_window, double* e_out);
+
 /* Log of the load-balancing calls made so far (by pic_step at its intervals
  * and by pic_rebalance), oldest first: copies min(max, n_total) entries into
  * out (host, nullable when max == 0) and the total count into *n_total. */

@@ -99,6 +99,7 @@ SIGNATURES = [
     ("pic_add_laser", _int, [_vp, ctypes.POINTER(LaserDesc)]),
     ("pic_set_field", _int, [_vp, _int, _vp, _int]),
     ("pic_set_gather", _int, [_vp, _int]),
+    ("pic_get_efficiency", _int, [_vp, _int, _int, ctypes.POINTER(ctypes.c_double)]),
     ("pic_set_lb_params", _int, [_vp, ctypes.POINTER(LBParams)]),
     ("pic_step", _int, [_vp, _int]),
     ("pic_sync", _int, [_vp]),

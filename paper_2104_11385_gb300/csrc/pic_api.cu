@@ -366,6 +366,15 @@ pic_status validate_lb(pic_sim* s, const pic_lb_params* p) {
 
 // the load-balancing routine (Sec. 2.2): costs -> proposed mapping -> E_old,
 // E_new -> adopt when E_new >= (1 + theta) E_old
+// E (Eq. 1) of the work-unit mapping in force for per-box costs; a box's
+// cost is divided evenly over its units
+double plan_efficiency(const pic_sim* s, const std::vector<double>& costs) {
+    const Plan& P = s->plan;
+    std::vector<double> uc(P.units.size());
+    for (size_t i = 0; i < P.units.size(); ++i) uc[i] = costs[P.units[i].box] / (double)P.units[i].nchunks;
+    return pic::lb_efficiency(uc.data(), P.unit_worker.data(), (int64_t)uc.size(), P.n_workers);
+}
+
 pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_result* out) {
     std::vector<double> costs;
     std::vector<int64_t> np;
@@ -373,14 +382,7 @@ pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_re
     const int64_t nb = s->h.nboxes;
     const int nw = n_workers_for(s, p);
     // E_old: the mapping in force, re-costed with the costs just measured
-    double e_old;
-    {
-        const Plan& P = s->plan;
-        std::vector<double> uc(P.units.size());
-        for (size_t i = 0; i < P.units.size(); ++i)
-            uc[i] = costs[P.units[i].box] / (double)P.units[i].nchunks;
-        e_old = pic::lb_efficiency(uc.data(), P.unit_worker.data(), (int64_t)uc.size(), P.n_workers);
-    }
+    const double e_old = plan_efficiency(s, costs);
     const int split = p.split > 0 ? p.split : s->split;
     std::vector<pic::Unit> units =
         pic::make_units(costs.data(), np.data(), nb, nw, split, 256, true);
@@ -942,6 +944,25 @@ pic_status pic_rebalance(pic_sim* s, const pic_lb_params* params, pic_lb_result*
             if (P.units[i].chunk == 0) assign_out[P.units[i].box] = P.unit_worker[i];
     }
     return check_device_error(s);
+}
+
+pic_status pic_get_efficiency(pic_sim* s, int strategy, int reset_window, double* e_out) {
+    TRY(check(s));
+    if (!e_out || (strategy != PIC_COST_HEURISTIC && strategy != PIC_COST_DEVICE_CLOCK &&
+                   strategy != PIC_COST_KERNEL_TIME))
+        return fail(s, PIC_EINVAL, "bad efficiency request");
+    TRY(ensure_ready(s));
+    TRY(sync_and_check(s));
+    std::vector<double> c;
+    std::vector<int64_t> np;
+    TRY(box_costs(s, strategy, s->lb.w_p, s->lb.w_c, c, np));
+    *e_out = plan_efficiency(s, c);
+    if (reset_window) {
+        CU(s, cudaMemsetAsync(s->h.cost_clock, 0, s->h.nboxes * sizeof(uint64_t), s->stream));
+        CU(s, cudaMemsetAsync(s->h.cost_time, 0, s->h.nboxes * sizeof(uint64_t), s->stream));
+        CU(s, cudaStreamSynchronize(s->stream));
+    }
+    return PIC_OK;
 }
 
 pic_status pic_get_lb_log(pic_sim* s, pic_lb_result* out, int64_t max, int64_t* n_total) {

@@ -123,6 +123,13 @@ class Simulation:
         kind = L.GATHER_ENERGY if energy_conserving else L.GATHER_MOMENTUM
         self._check(self._lib.pic_set_gather(self._h, kind))
 
+    def efficiency(self, cost=None, reset_window=False) -> float:
+        """E (Eq. 1) of the mapping in force over the current cost window."""
+        e = ctypes.c_double()
+        self._check(self._lib.pic_get_efficiency(self._h, L.COST_DEVICE_CLOCK if cost is None else int(cost),
+                                                 int(bool(reset_window)), ctypes.byref(e)))
+        return e.value
+
     def set_lb_params(self, **kw):
         self._check(self._lib.pic_set_lb_params(self._h, ctypes.byref(lb_params(**kw))))
 

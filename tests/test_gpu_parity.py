@@ -128,6 +128,25 @@ def test_lognormal_uneven_boxes_parity_with_balancing():
     assert all(0.0 < r["e_new"] <= 1.0 and r["adopted"] for r in log)  # theta 0: always adopted
 
 
+def test_efficiency_of_the_mapping_in_force():
+    """pic_get_efficiency reads the same cost window and mapping as the next
+    load-balancing call (its E_old), and a reset leaves an empty window
+    (all workers idle: E = 1)."""
+    wl = workloads.lognormal(seed=6, nbox=(4, 4, 4), box=8, median=800.0, sigma=1.5, order=1)
+    sim = make_gpu(wl)
+    sim.step(4)
+    e = sim.efficiency(pic.COST_DEVICE_CLOCK)
+    assert 0.0 < e < 1.0
+    r = sim.rebalance(mode=pic.LB_DYNAMIC, interval=10, theta=1e9, cost=pic.COST_DEVICE_CLOCK)
+    assert not r["adopted"] and r["e_old"] == e
+    sim.step(2)
+    e2 = sim.efficiency(pic.COST_DEVICE_CLOCK, reset_window=True)
+    assert 0.0 < e2 < 1.0
+    assert sim.efficiency(pic.COST_DEVICE_CLOCK) == 1.0
+    eh = sim.efficiency(pic.COST_HEURISTIC)
+    assert 0.0 < eh < 1.0
+
+
 @pytest.mark.parametrize("sched,policy,cost", [
     (pic.SCHED_LISTS, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
     (pic.SCHED_QUEUE, pic.POLICY_KNAPSACK, pic.COST_HEURISTIC),

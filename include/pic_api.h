@@ -211,6 +211,18 @@ pic_status pic_get_box_costs(pic_sim* sim, int strategy, double* costs_out, int6
 pic_status pic_rebalance(pic_sim* sim, const pic_lb_params* params, pic_lb_result* out,
                          int32_t* assign_out);
 
+/* In-kernel cost capture (Sec. 2.2, the device-side measurement this work
+ * is about): PIC_CAPTURE_CLOCK accumulates each thread's clock64() deltas
+ * over its particle loop into the box's device-clock cost; PIC_CAPTURE_TIME
+ * adds each work unit's %globaltimer span to the box's kernel-time cost.
+ * Both are on by default.  A strategy whose capture is off reads zero costs
+ * (and a load balancer driven by it then sees E = 1 and keeps its mapping);
+ * the heuristic strategy needs neither.  Turning capture off measures its
+ * overhead (the paper found CUPTI's about 2x).  Takes effect from the next
+ * step; synchronises.  Errors: PIC_EINVAL (mask outside 0..3). */
+enum { PIC_CAPTURE_CLOCK = 1, PIC_CAPTURE_TIME = 2 };
+pic_status pic_set_cost_capture(pic_sim* sim, int mask);
+
 /* E (Eq. 1, c_avg / c_max over workers) of the work-unit mapping in force,
  * with the per-box costs of the current cost window (strategy as in
  * pic_get_box_costs; a box's cost is divided evenly over its work units), as

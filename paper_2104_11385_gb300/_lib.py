@@ -58,6 +58,7 @@ class LaunchCfg(ctypes.Structure):
 
 PREC_FP64, PREC_FLOAT_FLOAT = 1, 2
 GATHER_MOMENTUM, GATHER_ENERGY = 0, 1
+CAPTURE_CLOCK, CAPTURE_TIME = 1, 2
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = [
     ("pic_add_laser", _int, [_vp, ctypes.POINTER(LaserDesc)]),
     ("pic_set_field", _int, [_vp, _int, _vp, _int]),
     ("pic_set_gather", _int, [_vp, _int]),
+    ("pic_set_cost_capture", _int, [_vp, _int]),
     ("pic_get_efficiency", _int, [_vp, _int, _int, ctypes.POINTER(ctypes.c_double)]),
     ("pic_set_lb_params", _int, [_vp, ctypes.POINTER(LBParams)]),
     ("pic_step", _int, [_vp, _int]),

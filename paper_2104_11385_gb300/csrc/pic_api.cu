@@ -607,6 +607,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     h.dim = g.dim;
     h.order = g.shape_order;
     h.absorb = g.absorb_cells;
+    h.capture = PIC_CAPTURE_CLOCK | PIC_CAPTURE_TIME;
     const int tdef = (g.dim == 3) ? 8 : 16;
     double inv2 = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -848,6 +849,18 @@ pic_status pic_set_gather(pic_sim* s, int kind) {
         TRY(pull_sim(s));
     }
     s->h.ec = kind == PIC_GATHER_ENERGY ? 1 : 0;
+    return upload_sim(s);
+}
+
+pic_status pic_set_cost_capture(pic_sim* s, int mask) {
+    TRY(check(s));
+    if (mask < 0 || mask > (PIC_CAPTURE_CLOCK | PIC_CAPTURE_TIME))
+        return fail(s, PIC_EINVAL, "bad capture mask %d", mask);
+    if (s->stepped) {
+        TRY(sync_and_check(s));
+        TRY(pull_sim(s));
+    }
+    s->h.capture = mask;
     return upload_sim(s);
 }
 

@@ -59,6 +59,7 @@ struct SimDev {
     CUtensorMap tmap[6];  // TMA descriptors of the padded E,B arrays (must stay first)
     int dim, order, nsp, absorb;
     int ec;               // 1: energy-conserving gather (order - 1 along staggered directions)
+    int capture;          // in-kernel cost capture: bit 0 clock64 (cost_clock), bit 1 %globaltimer (cost_time)
     int n[3];             // cells per direction
     int pn[3];            // padded extents (n + 2G; 1 for an inactive y)
     int g[3];             // guard width per direction (G or 0)

@@ -993,7 +993,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         if (u < 0) break;
         const UnitDev unit = sd->units[u];
         const SimDev& S = sims[unit.sim];
-        const uint64_t t_unit0 = threadIdx.x == 0 ? globaltimer() : 0ull;
+        const bool cap_clk = (S.capture & 1) != 0, cap_time = (S.capture & 2) != 0;
+        const uint64_t t_unit0 = (threadIdx.x == 0 && cap_time) ? globaltimer() : 0ull;
         const SmemPlan P = smem_plan(S.ebs, S.js);
         double* sEBd = smem;
         const R* sEB = reinterpret_cast<const R*>(smem);
@@ -1061,7 +1062,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         __syncthreads();
                     }
                 }
-                const unsigned long long c0 = clock64();
+                const unsigned long long c0 = cap_clk ? clock64() : 0ull;
                 {
                     // per-warp loop: no CTA barrier until the tile changes
                     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1090,19 +1091,22 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     }
                     __syncwarp();
                 }
-                my_clk += clock64() - c0;
+                if (cap_clk) my_clk += clock64() - c0;
             }
         }
         // in-situ cost: thread clocks -> warp sum -> shared -> one global add per unit
-        unsigned long long ws = warp_sum_u64(my_clk);
-        if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&s_cost, ws);
+        if (cap_clk) {
+            unsigned long long ws = warp_sum_u64(my_clk);
+            if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&s_cost, ws);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_cost) atomicAdd((unsigned long long*)(S.cost_clock + unit.box), s_cost);
             s_cost = 0ull;
             // kernel-time cost: wall span of the unit on this CTA (ns)
-            atomicAdd((unsigned long long*)(S.cost_time + unit.box),
-                      (unsigned long long)(globaltimer() - t_unit0));
+            if (cap_time)
+                atomicAdd((unsigned long long*)(S.cost_time + unit.box),
+                          (unsigned long long)(globaltimer() - t_unit0));
         }
     }
     if (cur.t >= 0) {

@@ -123,6 +123,11 @@ class Simulation:
         kind = L.GATHER_ENERGY if energy_conserving else L.GATHER_MOMENTUM
         self._check(self._lib.pic_set_gather(self._h, kind))
 
+    def set_cost_capture(self, clock=True, kernel_time=True):
+        """In-kernel cost capture: clock64 (device-clock cost) and %globaltimer (kernel-time cost)."""
+        mask = (L.CAPTURE_CLOCK if clock else 0) | (L.CAPTURE_TIME if kernel_time else 0)
+        self._check(self._lib.pic_set_cost_capture(self._h, mask))
+
     def efficiency(self, cost=None, reset_window=False) -> float:
         """E (Eq. 1) of the mapping in force over the current cost window."""
         e = ctypes.c_double()

@@ -123,6 +123,9 @@ def test_bad_arguments_are_status_codes():
     # destroying a null handle is a no-op
     assert lib.pic_destroy(None) == L.PIC_OK
     assert lib.pic_set_gather(None, 1) == L.PIC_EINVAL
+    assert lib.pic_set_cost_capture(None, 3) == L.PIC_EINVAL
+    e = ctypes.c_double()
+    assert lib.pic_get_efficiency(None, 1, 0, ctypes.byref(e)) == L.PIC_EINVAL
 
 
 def test_grid_validation_without_gpu():

@@ -147,6 +147,26 @@ def test_efficiency_of_the_mapping_in_force():
     assert 0.0 < eh < 1.0
 
 
+def test_cost_capture_switch():
+    """Capture off: no device-clock or kernel-time cost accumulates and the
+    physics is unchanged; capture on again: both accumulate."""
+    wl = workloads.random_plasma(79, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1, nspecies=1,
+                                 npart=5000, umax=1.0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_cost_capture(clock=False, kernel_time=False)
+    sim.step(3)
+    ref.step(3)
+    assert not sim.box_costs(pic.COST_DEVICE_CLOCK)[0].any()
+    assert not sim.box_costs(pic.COST_KERNEL_TIME)[0].any()
+    compare(sim, ref, wl)
+    sim.set_cost_capture(clock=True, kernel_time=False)
+    sim.step(2)
+    ref.step(2)
+    assert sim.box_costs(pic.COST_DEVICE_CLOCK)[0].sum() > 0
+    assert not sim.box_costs(pic.COST_KERNEL_TIME)[0].any()
+    compare(sim, ref, wl)
+
+
 @pytest.mark.parametrize("sched,policy,cost", [
     (pic.SCHED_LISTS, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
     (pic.SCHED_QUEUE, pic.POLICY_KNAPSACK, pic.COST_HEURISTIC),

@@ -181,13 +181,25 @@ class Simulation:
         self._check(self._lib.pic_num_particles(self._h, int(species), ctypes.byref(n)))
         return n.value
 
-    def particles(self, species=0) -> dict:
+    def particles(self, species=0, device=False) -> dict:
+        """A species' particles (x, y, z, ux, uy, uz, w, id) in the library's
+        order: numpy arrays, or torch tensors on the GPU with device=True."""
         n = self.num_particles(species)
         names = ("x", "y", "z", "ux", "uy", "uz", "w")
-        out = {k: np.empty(n, np.float64) for k in names}
-        ids = np.empty(n, np.int64)
-        ptrs = (ctypes.c_void_p * 7)(*[ctypes.c_void_p(out[k].ctypes.data) for k in names])
-        self._check(self._lib.pic_read_particles(self._h, int(species), ptrs, ctypes.c_void_p(ids.ctypes.data), 0))
+        if device:
+            import torch
+            out = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in names}
+            ids = torch.empty(n, dtype=torch.int64, device="cuda")
+            addr = {k: out[k].data_ptr() for k in names}
+            id_addr = ids.data_ptr()
+        else:
+            out = {k: np.empty(n, np.float64) for k in names}
+            ids = np.empty(n, np.int64)
+            addr = {k: out[k].ctypes.data for k in names}
+            id_addr = ids.ctypes.data
+        ptrs = (ctypes.c_void_p * 7)(*[ctypes.c_void_p(addr[k]) for k in names])
+        self._check(self._lib.pic_read_particles(self._h, int(species), ptrs, ctypes.c_void_p(id_addr),
+                                                 1 if device else 0))
         out["id"] = ids
         return out
 

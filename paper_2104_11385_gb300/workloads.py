@@ -21,7 +21,7 @@ particle counts):
                  dx = 0.25), box particle counts round(exp(N(ln 2000, 2^2))),
                  uniform positions inside the box, u ~ N(0, 0.01^2), weights for
                  a mean density n0 = 1, quadratic shape, periodic.
-  foil_scale     3D laser-foil at scale: 512 x 512 x 1024 cells in 32^3 boxes,
+  foil_at_scale  3D laser-foil at scale: 512 x 512 x 1024 cells in 32^3 boxes,
                  foil 16 cells thick at 64 ppc per species.
   laser_ion_2d   the paper's 2D3V laser-ion setup (Sec. 3.1) at one-GPU scale:
                  (z, x) domain 30 um x 30 um (z in [-10, 20] um, x in [-15, 15]
@@ -100,6 +100,15 @@ def foil(seed=2, n=(256, 256, 256), box=32, foil_z=(128, 136), ppc=64, density=3
         "dx": (dx, dx, dx), "dt": 0.99 * dx / math.sqrt(3.0), "order": order, "absorb": absorb,
         "species": [e, p], "laser": laser, "rho0": 0.0, "steps": 1000, "lb_interval": 10,
     }
+
+
+def foil_at_scale(seed=5):
+    """The foil at scale: 512 x 512 x 1024 cells in 32^3 boxes, the foil 16
+    cells thick (z in [512, 528)) at 64 ppc per species (536,870,912
+    particles); 2000 steps into the expansion, balancing every 20."""
+    wl = foil(seed=seed, n=(512, 512, 1024), box=32, foil_z=(512, 528), ppc=64)
+    wl["steps"], wl["lb_interval"] = 2000, 20
+    return wl
 
 
 def foil256(seed=2, scale=1):

@@ -184,3 +184,14 @@ def test_foil_at_scale_full_size_region():
     sim, tuned = bench_state(wl)
     check_regions(sim, wl, [((240, 240, 508), (264, 264, 532))])
     sim.close()
+
+
+def test_laser_ion_2d_full_size_region():
+    """The paper's 2D3V laser-ion setup at one-GPU scale (1920^2 cells, 40M
+    particles, cubic shapes): a region across the target edge and a box
+    boundary."""
+    wl = workloads.laser_ion_2d()
+    sim, tuned = bench_state(wl)
+    # target centre at (x, z) = (960, 640) cells, core radius 320 cells; 64^2 boxes
+    check_regions(sim, wl, [((1000, 0, 300), (1040, 1, 340))])
+    sim.close()

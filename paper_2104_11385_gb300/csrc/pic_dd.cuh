@@ -14,16 +14,19 @@ struct dd {
 };
 
 // ---- error-free transformations
+// Every FP32 step is an explicit round-to-nearest intrinsic: the compiler
+// contracts a plain a * b + c into one FMA, which would let a sum see an
+// unrounded product and break the exactness these transformations rely on.
 __device__ __forceinline__ dd dd_two_sum(float a, float b) {
-    const float s = a + b;
-    const float v = s - a;
-    const float e = (a - (s - v)) + (b - v);
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
     return dd{s, e};
 }
 
 __device__ __forceinline__ dd dd_quick_two_sum(float a, float b) {  // |a| >= |b|
-    const float s = a + b;
-    return dd{s, b - (s - a)};
+    const float s = __fadd_rn(a, b);
+    return dd{s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
 // ---- conversions
@@ -55,13 +58,14 @@ __device__ __forceinline__ dd dd_from(double x) {
     return dd{h, __double2float_rn(x - (double)h)};
 }
 
-// float-float -> double by integer work: hi widened exactly (exponent rebias,
-// mantissa << 29), lo added in units of the double ulp of hi (truncated), with
-// the pattern arithmetic of dd_from; a hi that is a power of two and a lo of
-// the other sign land in the binade below, where the unit is half as large.
-// Needs |lo| <= 2^5 ulp_double(hi) (every normalised pair); other pairs, and a
-// hi or lo outside the normal float range, take the FP64 route.
+// float-float -> double by integer work, after one normalising TwoSum: hi
+// widened exactly (exponent rebias, mantissa << 29), lo added in units of the
+// double ulp of hi (truncated), with the pattern arithmetic of dd_from; a hi
+// that is a power of two and a lo of the other sign land in the binade below,
+// where the unit is half as large.  A hi or lo outside the normal float range
+// takes the FP64 route.
 __device__ __forceinline__ double dd_to(dd a) {
+    a = dd_two_sum(a.h, a.l);
     const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
     const int he = (int)((hb >> 23) & 0xFFu), le = (int)((lb >> 23) & 0xFFu);
     if (he >= 1 && he <= 254) {
@@ -83,11 +87,12 @@ __host__ __device__ constexpr dd dd_const(double x) {
     return dd{static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x)))};
 }
 
-// float-float -> double for a normalised pair (|lo| <= ulp(hi)/2), branch-
-// free: the form dd_to takes in the current deposit, where it runs dozens of
-// times per particle.  Float subnormals flush to zero (|hi| below 2^-126
+// float-float -> double, branch-free after one normalising TwoSum: the form
+// dd_to takes in the current deposit, where it runs dozens of times per
+// particle.  Float subnormals flush to zero (|hi| below 2^-126
 // gives 0, a subnormal lo is dropped: an absolute error below 2^-126).
 __device__ __forceinline__ double dd_to_norm(dd a) {
+    a = dd_two_sum(a.h, a.l);
     const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
     const unsigned ha = hb & 0x7FFFFFFFu;
     unsigned long long mag = ((unsigned long long)ha + (896ull << 23)) << 29;
@@ -102,24 +107,30 @@ __device__ __forceinline__ double dd_to_norm(dd a) {
 }
 
 // ---- arithmetic
+// Chained operations leave the pair unnormalised (|lo| may reach a few
+// ulp(hi)): TwoSum and TwoProd are exact for any operands, so the value stays
+// hi + lo to about 2^-46 relative while each add saves 3 instructions and
+// each product 3.  dd_norm (a TwoSum, exact whatever the magnitudes)
+// restores |lo| <= ulp(hi)/2 where a conversion or an estimate needs it.
+__device__ __forceinline__ dd dd_norm(dd a) { return dd_two_sum(a.h, a.l); }
 __device__ __forceinline__ dd operator+(dd a, dd b) {
-    dd s = dd_two_sum(a.h, b.h);
-    s.l += a.l + b.l;
-    return dd_quick_two_sum(s.h, s.l);
+    const dd s = dd_two_sum(a.h, b.h);
+    return dd{s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
 }
 __device__ __forceinline__ dd operator-(dd a) { return dd{-a.h, -a.l}; }
 __device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
 __device__ __forceinline__ dd operator*(dd a, dd b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
-    return dd_quick_two_sum(p, e);
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    return dd{p, e};
 }
 // a * b + c
 __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return a * b + c; }
 
 // 1/sqrt(x): FP32 estimate refined by one Newton step in float-float
 __device__ __forceinline__ dd dd_rsqrt(dd x) {
+    x = dd_norm(x);
     const float y0 = rsqrtf(x.h);
     const dd y{y0, 0.0f};
     const dd r = dd_const(1.0) - x * (y * y);  // residual ~ 2^-22
@@ -128,6 +139,7 @@ __device__ __forceinline__ dd dd_rsqrt(dd x) {
 
 // 1/x: FP32 estimate refined by one Newton step in float-float
 __device__ __forceinline__ dd dd_rcp(dd x) {
+    x = dd_norm(x);
     const float y0 = __frcp_rn(x.h);
     const dd y{y0, 0.0f};
     const dd r = dd_const(1.0) - x * y;

@@ -30,6 +30,15 @@ __device__ __forceinline__ dd dd_quick_two_sum(float a, float b) {  // |a| >= |b
 }
 
 // ---- conversions
+// The FP64 routes of the conversions below are separate functions: inlined,
+// the compiler predicates them and their FP64 instructions (which include the
+// double <-> float conversions) then occupy the FP64 pipe on every call.
+static __device__ __noinline__ dd dd_from_slow(double x) {
+    const float h = __double2float_rn(x);
+    return dd{h, __double2float_rn(x - (double)h)};
+}
+static __device__ __noinline__ double dd_to_slow(float h, float l) { return (double)h + (double)l; }
+
 // double -> float-float by integer work on the IEEE-754 bits (every FP64
 // instruction, conversions included, issues at the FP64 rate): hi is x rounded
 // to 24 bits (ties away from zero on the magnitude), lo the remainder in units
@@ -54,8 +63,7 @@ __device__ __forceinline__ dd dd_from(double x) {
         return dd{h, l};
     }
     if (u == 0ull) return dd{__uint_as_float(sgn), 0.0f};
-    const float h = __double2float_rn(x);
-    return dd{h, __double2float_rn(x - (double)h)};
+    return dd_from_slow(x);
 }
 
 // float-float -> double by integer work, after one normalising TwoSum: hi
@@ -72,7 +80,7 @@ __device__ __forceinline__ double dd_to(dd a) {
         unsigned long long mag = ((unsigned long long)(hb & 0x7FFFFFFFu) + (896ull << 23)) << 29;
         if ((lb & 0x7FFFFFFFu) != 0u) {
             int sh = le - he + 29;
-            if (le == 0 || sh > 5) return (double)a.h + (double)a.l;
+            if (le == 0 || sh > 5) return dd_to_slow(a.h, a.l);
             const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
             const bool sub = ((hb ^ lb) & 0x80000000u) != 0u;
             if (sub && (hb & 0x7FFFFFu) == 0u) sh += 1;
@@ -81,7 +89,7 @@ __device__ __forceinline__ double dd_to(dd a) {
         }
         return __longlong_as_double((long long)(mag | ((unsigned long long)(hb & 0x80000000u) << 32)));
     }
-    return (double)a.h + (double)a.l;
+    return dd_to_slow(a.h, a.l);
 }
 __host__ __device__ constexpr dd dd_const(double x) {
     return dd{static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x)))};

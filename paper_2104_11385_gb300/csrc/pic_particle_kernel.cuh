@@ -83,7 +83,19 @@ __device__ __forceinline__ void fence_proxy_async() {
 // Exact floor and fractional part of x.  On GB300 every FP64 instruction,
 // conversions included, issues at the FP64 rate (about 2 per SM per clock), so
 // for 0 <= x < 2^31 both come from integer work on the IEEE-754 bits; other x
-// go through floor().  Both routes give the identical (exact) results.
+// go through floor().  Both routes give the identical (exact) results.  The
+// floor() route is a separate function: inlined, the compiler predicates it,
+// and its FP64 instructions then occupy the FP64 pipe on every call.
+struct IFrac {
+    int i;
+    double f;
+};
+static __device__ __noinline__ IFrac ifloor_frac_slow(double x) {
+    const double fl = floor(x);
+    return IFrac{(int)fl, x - fl};
+}
+static __device__ __noinline__ int ifloor_slow(double x) { return (int)floor(x); }
+
 __device__ __forceinline__ int ifloor_frac(double x, double& f) {
     const long long b = __double_as_longlong(x);
     const int e = (int)((unsigned long long)b >> 52) - 1023;  // sign set -> e > 1023
@@ -107,9 +119,9 @@ __device__ __forceinline__ int ifloor_frac(double x, double& f) {
         }
         return i;
     }
-    const double fl = floor(x);
-    f = x - fl;
-    return (int)fl;
+    const IFrac r = ifloor_frac_slow(x);
+    f = r.f;
+    return r.i;
 }
 
 // floor of x >= 0 (x < 2^31) by integer work; floor() otherwise
@@ -119,7 +131,7 @@ __device__ __forceinline__ int ifloor(double x) {
     if (e < 0 && b >= 0) return 0;
     if (e >= 0 && e < 31)
         return (int)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) >> (52 - e));
-    return (int)floor(x);
+    return ifloor_slow(x);
 }
 
 // x < 0 and x >= y for y > 0 by integer comparison of the bit patterns

@@ -43,16 +43,16 @@ BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 
 # DRAM traffic of the FP64 particle kernel <3,1> from one ncu capture on the
 # foil recipe at half extents (128^3 cells, 8,388,608 particles; 256 threads,
-# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 508.01 + 415.84 MB
+# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 508.07 + 413.95 MB
 # (the capture's summary sits with the ncu profiles).  Traffic grows with the
 # particle count, so a full launch is scaled by particles.  The figure is reported only
 # while the kernel sources hash to what was captured.
-TRAFFIC_CAPTURE = {"bytes_per_particle": (508.011520e6 + 415.840256e6) / 8388608, "dim": 3, "order": 1,
+TRAFFIC_CAPTURE = {"bytes_per_particle": (508.073216e6 + 413.951232e6) / 8388608, "dim": 3, "order": 1,
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
                                "paper_2104_11385_gb300/csrc/pic_particles_f64.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h"),
-                   "sha256": "2c7aa1394cf4d7ecdce0f244b80fe33ef5bab00bcac870490775e796970b5035"}
+                   "sha256": "093be11348d8d06b97a999387145ccb9c3251dc329fe8747898ff176804d7e3b"}
 
 
 def _kernel_sources_sha(paths):

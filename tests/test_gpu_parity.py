@@ -125,7 +125,10 @@ def test_lognormal_uneven_boxes_parity_with_balancing():
     compare(sim, ref, wl)
     log = sim.lb_log()
     assert len(log) == 3  # steps 3, 6, 9
-    assert all(0.0 < r["e_new"] <= 1.0 and r["adopted"] for r in log)  # theta 0: always adopted
+    # theta 0: adopted exactly when the proposal is at least as good (greedy
+    # knapsack is not optimal, so a proposal can be worse than the mapping in force)
+    assert all(0.0 < r["e_new"] <= 1.0 and r["adopted"] == (r["e_new"] >= r["e_old"]) for r in log)
+    assert any(r["adopted"] for r in log)
 
 
 def test_efficiency_of_the_mapping_in_force():

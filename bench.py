@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import math
+import re
 import os
 import statistics
 import subprocess
@@ -45,22 +46,28 @@ BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 # foil recipe at half extents (128^3 cells, 8,388,608 particles; 256 threads,
 # 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 508.07 + 413.95 MB
 # (the capture's summary sits with the ncu profiles).  Traffic grows with the
-# particle count, so a full launch is scaled by particles.  The figure is reported only
-# while the kernel sources hash to what was captured.
+# particle count, so a full launch is scaled by particles.  The figure is
+# reported only while the kernel's code (comments aside) hashes to what was
+# captured.
 TRAFFIC_CAPTURE = {"bytes_per_particle": (508.073216e6 + 413.951232e6) / 8388608, "dim": 3, "order": 1,
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
                                "paper_2104_11385_gb300/csrc/pic_particles_f64.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h"),
-                   "sha256": "093be11348d8d06b97a999387145ccb9c3251dc329fe8747898ff176804d7e3b"}
+                   "sha256": "abc0f8170601b86592345abf76b59387f7af15abf49b2872fb50f4320df0c6f5"}
 
 
 def _kernel_sources_sha(paths):
+    """SHA-256 of the kernel's code: comments, blank lines and trailing blanks
+    dropped, so that a comment edit does not count as a kernel change."""
     h = hashlib.sha256()
     here = os.path.dirname(os.path.abspath(__file__))
     for rel in paths:
-        with open(os.path.join(here, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(here, rel)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()
 
 

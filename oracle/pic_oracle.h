@@ -12,7 +12,10 @@
  *   - the explicit PIC cycle of Sec. 2.1 (Maxwell on cells, Lorentz push of
  *     weighted markers, deposited currents), with the schemes the paper leaves
  *     open fixed as: Yee staggering, relativistic Boris push, Esirkepov
- *     charge-conserving deposit, linear or quadratic B-spline shapes;
+ *     charge-conserving deposit, B-spline shapes of order 1, 2 or 3 (the
+ *     paper's runs use order 3, Sec. 3.1), gathered with the same order in
+ *     every direction or, energy-conserving, one order lower along each
+ *     component's staggered directions;
  *   - the load-balance efficiency E = c_avg / c_max (Sec. 2.2, Eq. 1), the
  *     knapsack and Morton space-filling-curve policies (Sec. 2.2), the
  *     improvement threshold (Sec. 2.2, Sec. 3.2) and the performance model

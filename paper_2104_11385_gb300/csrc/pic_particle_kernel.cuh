@@ -15,8 +15,11 @@
 // tile key and the per-tile histogram for the re-sort.
 //
 // Physics per particle (the schemes the paper leaves open, Sec. 2.1): field
-// gather with B-spline shapes at each component's Yee location, relativistic
-// Boris push, Esirkepov charge-conserving deposit (Esirkepov 2001).
+// gather with B-spline shapes of order 1-3 at each component's Yee location
+// (same order in every direction, or the energy-conserving variant with one
+// order less along the staggered directions), relativistic Boris push,
+// Esirkepov charge-conserving deposit (Esirkepov 2001).  The cost capture can
+// be switched off per simulation to measure its overhead.
 #pragma once
 #include <type_traits>
 

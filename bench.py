@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--no-cost-arms", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--server-requests", type=int, default=48)
+    ap.add_argument("--server-steps-max", type=int, default=400,
+                    help="request lengths U[100, max] steps (the serving recipe's full range is 2000)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--timeline", type=int, default=0,
                     help="instead of the bench line: N steps of the workload under each load-balancing mode "
@@ -465,8 +467,8 @@ def run_c3(args, steps=10):
 
 def run_server(args, seed=4):
     """Serving arm: independent 2D3V thermal-plasma requests (grid side in
-    {64,128,256,512}, ppc in {1,..,64}, steps U[100, 400]: the serving workload
-    with shortened runs) through the continuous-batching server; first all at
+    {64,128,256,512}, ppc in {1,..,64}, steps U[100, max]; max = 400 by default,
+    the serving workload with shortened runs, 2000 for the full recipe) through the continuous-batching server; first all at
     once (saturated throughput), then Poisson arrivals at 0.8x and 0.5x that
     rate."""
     import numpy as np
@@ -478,7 +480,7 @@ def run_server(args, seed=4):
     for i in range(n):
         side = int(rng.choice([64, 128, 256, 512]))
         ppc = int(rng.choice([1, 2, 4, 8, 16, 32, 64]))
-        steps = int(rng.integers(100, 401))
+        steps = int(rng.integers(100, args.server_steps_max + 1))
         reqs.append(dict(ncell=(side, 1, side), box=(32, 1, 32), dx=(0.2, 1.0, 0.2), nsteps=steps,
                          plasma=dict(ppc=ppc, density=1.0, u_th=0.02, ripple=0.01, seed=1000 + i)))
     work = sum(r["ncell"][0] * r["ncell"][2] * r["plasma"]["ppc"] * r["nsteps"] for r in reqs)
@@ -509,7 +511,8 @@ def run_server(args, seed=4):
 
     wall_sat, lat_sat, st_sat = serve([0.0] * n)
     sat_rate = n / wall_sat
-    out = {"requests": n, "mix": "2D3V, side {64..512}, ppc {1..64}, steps U[100,400], 32x32 boxes",
+    out = {"requests": n,
+           "mix": "2D3V, side {64..512}, ppc {1..64}, steps U[100,%d], 32x32 boxes" % args.server_steps_max,
            "saturated_requests_per_s": sat_rate, "saturated_particle_updates_per_s": work / wall_sat}
     for frac in (0.8, 0.5):
         lam = frac * sat_rate

@@ -53,7 +53,8 @@ TRAFFIC_CAPTURE = {"bytes_per_particle": (508.073216e6 + 413.951232e6) / 8388608
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
                                "paper_2104_11385_gb300/csrc/pic_particles_f64.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
-                               "paper_2104_11385_gb300/csrc/pic_internal.h"),
+                               "paper_2104_11385_gb300/csrc/pic_internal.h",
+                               "paper_2104_11385_gb300/csrc/pic_sync.cuh"),
                    "sha256": "abc0f8170601b86592345abf76b59387f7af15abf49b2872fb50f4320df0c6f5"}
 
 

@@ -131,6 +131,22 @@ pic_status pic_set_field(pic_sim* sim, int comp, const double* data, int on_devi
 enum { PIC_GATHER_MOMENTUM = 0, PIC_GATHER_ENERGY = 1 };
 pic_status pic_set_gather(pic_sim* sim, int kind);
 
+/* Sets the step counter n (time t = n dt, which the laser antenna reads, and
+ * the count that load-balancing intervals refer to), for resuming a run from
+ * saved state: pic_init + pic_add_species with the saved arrays and ids +
+ * pic_set_field for E and B + pic_set_step.  Synchronises.  Errors:
+ * PIC_EINVAL (step < 0). */
+pic_status pic_set_step(pic_sim* sim, int64_t step);
+
+/* Self-test of the device-side bounded wait (every wait in the kernels is
+ * bounded by %globaltimer so that a lost arrival cannot hang the GPU): one CTA
+ * waits on an mbarrier that nothing arrives at, gives up after limit_ns
+ * (1e3..5e9), records the error and returns.  Expected result: PIC_ETIMEOUT,
+ * with the handle poisoned like after any device-side error (later calls
+ * return PIC_ESTATE; pic_destroy still works and other handles are
+ * unaffected).  Errors: PIC_EINVAL (limit out of range). */
+pic_status pic_selftest_bounded_wait(pic_sim* sim, int64_t limit_ns);
+
 /* ---- load balancing (Sec. 2.2) ------------------------------------------- */
 enum { PIC_POLICY_KNAPSACK = 0, PIC_POLICY_SFC = 1 };
 enum { PIC_COST_HEURISTIC = 0, PIC_COST_DEVICE_CLOCK = 1, PIC_COST_KERNEL_TIME = 2 };
@@ -177,6 +193,7 @@ typedef struct {
     int adopted;
     int64_t n_units;
     double predicted_speedup;
+    int64_t step; /* steps completed when the call ran */
 } pic_lb_result;
 
 /* Stores load-balancing parameters used by pic_step (default: mode NONE). */

@@ -49,7 +49,7 @@ class LBParams(ctypes.Structure):
 
 class LBResult(ctypes.Structure):
     _fields_ = [("e_old", _d), ("e_new", _d), ("adopted", _int), ("n_units", _i64),
-                ("predicted_speedup", _d)]
+                ("predicted_speedup", _d), ("step", _i64)]
 
 
 class LaunchCfg(ctypes.Structure):
@@ -100,6 +100,8 @@ SIGNATURES = [
     ("pic_add_laser", _int, [_vp, ctypes.POINTER(LaserDesc)]),
     ("pic_set_field", _int, [_vp, _int, _vp, _int]),
     ("pic_set_gather", _int, [_vp, _int]),
+    ("pic_set_step", _int, [_vp, _i64]),
+    ("pic_selftest_bounded_wait", _int, [_vp, _i64]),
     ("pic_set_cost_capture", _int, [_vp, _int]),
     ("pic_get_efficiency", _int, [_vp, _int, _int, ctypes.POINTER(ctypes.c_double)]),
     ("pic_set_lb_params", _int, [_vp, ctypes.POINTER(LBParams)]),

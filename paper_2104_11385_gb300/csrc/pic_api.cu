@@ -183,6 +183,8 @@ pic_status check_device_error(pic_sim* s) {
     CU(s, cudaStreamSynchronize(s->stream));
     if (e & PIC_DERR_TMA_TIMEOUT)
         return fail(s, PIC_ETIMEOUT, "a bounded wait on a TMA tile load ran out (device error %d)", e);
+    if (e & PIC_DERR_WAIT_TIMEOUT)
+        return fail(s, PIC_ETIMEOUT, "the bounded-wait self-test ran out, as designed (device error %d)", e);
     if (e) return fail(s, PIC_ECUDA, "device-side check failed (device error word %d)", e);
     return PIC_OK;
 }
@@ -413,6 +415,7 @@ pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_re
     r.adopted = adopted ? 1 : 0;
     r.n_units = (int64_t)units.size();
     r.predicted_speedup = pic::predicted_speedup(e_old > 0 ? e_old : 1.0, s->h.dim == 3 ? 0.88 : 0.91);
+    r.step = s->step_count;
     s->lb_log.push_back(r);
     if (out) *out = r;
     return PIC_OK;
@@ -862,6 +865,24 @@ pic_status pic_set_cost_capture(pic_sim* s, int mask) {
     }
     s->h.capture = mask;
     return upload_sim(s);
+}
+
+pic_status pic_selftest_bounded_wait(pic_sim* s, int64_t limit_ns) {
+    TRY(check(s));
+    if (limit_ns < 1000 || limit_ns > 5000000000ll)
+        return fail(s, PIC_EINVAL, "limit_ns must be in [1e3, 5e9]");
+    CU(s, pic_launch_selftest_wait(s->hs.err, (uint64_t)limit_ns, s->stream));
+    return sync_and_check(s);
+}
+
+pic_status pic_set_step(pic_sim* s, int64_t step) {
+    TRY(check(s));
+    if (step < 0) return fail(s, PIC_EINVAL, "step must be >= 0");
+    TRY(sync_and_check(s));
+    CU(s, cudaMemcpyAsync(s->h.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));
+    CU(s, cudaStreamSynchronize(s->stream));
+    s->step_count = step;
+    return PIC_OK;
 }
 
 pic_status pic_set_lb_params(pic_sim* s, const pic_lb_params* p) {

@@ -3,6 +3,7 @@
 // swap), end-of-step bookkeeping, initial keys, per-box counts, and the
 // dispatch of the particle kernel over its two arithmetic variants.
 #include "pic_internal.h"
+#include "pic_sync.cuh"
 
 namespace {
 
@@ -253,5 +254,22 @@ cudaError_t pic_launch_to_cells(double* p, int64_t np, double d, int n, cudaStre
 cudaError_t pic_launch_from_cells(const double* src, double* dst, int64_t np, double d,
                                   cudaStream_t st) {
     if (np > 0) pic_scale_copy_kernel<<<grid_for(np, 256), 256, 0, st>>>(src, dst, np, d);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// bounded-wait self-test: the particle kernel's mbarrier wait on a barrier that
+// nothing arrives at.  It must give up after limit_ns, record the error and
+// return, leaving the context usable.
+// ---------------------------------------------------------------------------
+__global__ void pic_selftest_wait_kernel(int32_t* err, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, limit_ns)) atomicOr(err, PIC_DERR_WAIT_TIMEOUT);
+}
+
+cudaError_t pic_launch_selftest_wait(int32_t* err, uint64_t limit_ns, cudaStream_t st) {
+    pic_selftest_wait_kernel<<<1, 32, 0, st>>>(err, limit_ns);
     return cudaGetLastError();
 }

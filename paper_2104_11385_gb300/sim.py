@@ -118,6 +118,14 @@ class Simulation:
         p, dev, k = _ptr(data if type(data).__module__.startswith("torch") else np.asarray(data, np.float64))
         self._check(self._lib.pic_set_field(self._h, int(comp), p, dev))
 
+    def set_step(self, step: int):
+        """Sets the step counter (time t = step * dt), for resuming from saved state."""
+        self._check(self._lib.pic_set_step(self._h, int(step)))
+
+    def selftest_bounded_wait(self, limit_ns: int):
+        """Runs the device bounded-wait self-test; raises PicError(PIC_ETIMEOUT) as designed."""
+        self._check(self._lib.pic_selftest_bounded_wait(self._h, int(limit_ns)))
+
     def set_gather(self, energy_conserving: bool):
         """Energy-conserving (order - 1 along staggered directions) or default field gather."""
         kind = L.GATHER_ENERGY if energy_conserving else L.GATHER_MOMENTUM
@@ -157,7 +165,7 @@ class Simulation:
         self._check(self._lib.pic_rebalance(self._h, ctypes.byref(lb_params(**kw)), ctypes.byref(r),
                                             a.ctypes.data_as(L._pi32)))
         return {"e_old": r.e_old, "e_new": r.e_new, "adopted": bool(r.adopted), "n_units": r.n_units,
-                "predicted_speedup": r.predicted_speedup, "assign": a}
+                "predicted_speedup": r.predicted_speedup, "step": r.step, "assign": a}
 
     def lb_log(self) -> list:
         n = ctypes.c_int64()
@@ -165,7 +173,7 @@ class Simulation:
         buf = (L.LBResult * max(n.value, 1))()
         self._check(self._lib.pic_get_lb_log(self._h, buf, n.value, ctypes.byref(n)))
         return [{"e_old": r.e_old, "e_new": r.e_new, "adopted": bool(r.adopted), "n_units": r.n_units,
-                 "predicted_speedup": r.predicted_speedup} for r in buf[:n.value]]
+                 "predicted_speedup": r.predicted_speedup, "step": r.step} for r in buf[:n.value]]
 
     def read_field(self, comp, out=None):
         if out is None:

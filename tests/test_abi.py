@@ -5,6 +5,7 @@ import ctypes
 import json
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -37,10 +38,38 @@ def test_library_exports_every_declared_symbol():
     assert declared <= bound | {"pic_last_error"}, declared - bound
 
 
-def test_struct_layouts_match_header_sizes():
-    # offsets the C side relies on: int64 fields must be 8-aligned
-    assert ctypes.sizeof(L.GridDesc) == 4 + 4 + 24 + 12 + 4 + 24 + 8 + 8 + 4 + 4 + 8
-    assert ctypes.sizeof(L.LBParams) == 4 + 4 + 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4 + 4 + 4
+STRUCTS = [("pic_grid_desc", "GridDesc"), ("pic_laser_desc", "LaserDesc"), ("pic_lb_params", "LBParams"),
+           ("pic_lb_result", "LBResult"), ("pic_launch_cfg", "LaunchCfg"), ("pic_stats", "Stats"),
+           ("pic_server_desc", "ServerDesc"), ("pic_plasma_init", "PlasmaInit"),
+           ("pic_species_init", "SpeciesInit"), ("pic_request_desc", "RequestDesc"),
+           ("pic_server_stats", "ServerStats")]
+
+
+def test_struct_layouts_match_the_headers(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (gcc on this host)."""
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pic_api.h"', '#include "pic_server.h"',
+             "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        lines.append(f'    printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in getattr(L, pyname)._fields_:
+            lines.append(f'    printf("{pyname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, v = ln.split()
+            got[(a, b)] = int(v)
+    for cname, pyname in STRUCTS:
+        cls = getattr(L, pyname)
+        assert got[(pyname, "size")] == ctypes.sizeof(cls), pyname
+        for fname, _ in cls._fields_:
+            assert got[(pyname, fname)] == getattr(cls, fname).offset, (pyname, fname)
 
 
 def _random_case(rng, nb, dim):

@@ -124,7 +124,7 @@ def test_lognormal_uneven_boxes_parity_with_balancing():
     ref.step(10)
     compare(sim, ref, wl)
     log = sim.lb_log()
-    assert len(log) == 3  # steps 3, 6, 9
+    assert [r["step"] for r in log] == [3, 6, 9]
     # theta 0: adopted exactly when the proposal is at least as good (greedy
     # knapsack is not optimal, so a proposal can be worse than the mapping in force)
     assert all(0.0 < r["e_new"] <= 1.0 and r["adopted"] == (r["e_new"] >= r["e_old"]) for r in log)
@@ -379,3 +379,57 @@ def test_gather_kind_switch_between_steps():
     compare(sim, ref, wl)
     with pytest.raises(pic.PicError):
         sim._check(sim._lib.pic_set_gather(sim._h, 7))
+
+
+def test_bounded_wait_selftest_times_out_and_poisons_only_its_handle():
+    """The device's bounded wait gives up on an mbarrier that nothing arrives
+    at, the host reads PIC_ETIMEOUT and poisons that handle; the context stays
+    usable and a fresh handle still matches the oracle."""
+    wl = workloads.random_plasma(401, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1, nspecies=1,
+                                 npart=2000, umax=0.5)
+    sim = make_gpu(wl)
+    sim.step(1)
+    with pytest.raises(pic.PicError) as err:
+        sim.selftest_bounded_wait(20_000_000)  # 20 ms
+    assert err.value.status == pic._lib.PIC_ETIMEOUT
+    with pytest.raises(pic.PicError) as err2:
+        sim.step(1)
+    assert err2.value.status == pic._lib.PIC_ESTATE
+    sim.close()
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.step(3)
+    ref.step(3)
+    compare(sim, ref, wl)
+
+
+def test_resume_from_saved_state_matches_the_continuous_run():
+    """Checkpoint / resume through the public calls: particles (with ids) and
+    E, B read after 5 steps, a new handle built from them with the step counter
+    set, 5 more steps; the laser antenna and absorbing layers make the step
+    counter and the particle set matter."""
+    wl = workloads.random_plasma(402, 3, (16, 16, 48), (8, 8, 16), (0.3, 0.3, 0.3), 2, nspecies=2, npart=3000,
+                                 umax=2.0, absorb=6, laser=True)
+    a = make_gpu(wl)
+    a.step(10)
+    b = make_gpu(wl)
+    b.step(5)
+    saved = [b.particles(s) for s in range(len(wl["species"]))]
+    fields = [b.read_field(c) for c in range(6)]
+    b.close()
+    wl2 = dict(wl)
+    wl2["species"] = [dict(sp, **{k: saved[s][k] for k in ("x", "y", "z", "ux", "uy", "uz", "w", "id")})
+                      for s, sp in enumerate(wl["species"])]
+    c = make_gpu(wl2, fields)
+    c.set_step(5)
+    c.step(5)
+    a.sync()
+    c.sync()
+    for comp in range(9):
+        got, want = c.read_field(comp).reshape(-1), a.read_field(comp).reshape(-1)
+        assert rel(got, want) <= TOL, comp
+    for s in range(len(wl["species"])):
+        g, r = c.particles(s), a.particles(s)
+        gi, ri = np.argsort(g["id"]), np.argsort(r["id"])
+        assert np.array_equal(g["id"][gi], r["id"][ri])
+        for k in ("x", "y", "z", "ux", "uy", "uz"):
+            assert rel(g[k][gi], r[k][ri]) <= TOL, (s, k)

@@ -762,21 +762,25 @@ pic_status pic_add_species(pic_sim* s, double charge, double mass, int64_t np,
     CU(s, cudaMemsetAsync(sp.off, 0, (h.ntiles + 2) * sizeof(int64_t), s->stream));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (np > 0) {
+        // the input lands in the alternate buffers and is gathered into the
+        // current ones in a scrambled order (see pic_launch_permute)
         for (int a = 0; a < 7; ++a) {
             if (a == 1 && h.dim == 2) {
                 CU(s, cudaMemsetAsync(sp.cur[1], 0, np * sizeof(double), s->stream));
                 continue;
             }
-            CU(s, cudaMemcpyAsync(sp.cur[a], soa[a], np * sizeof(double), kind, s->stream));
+            CU(s, cudaMemcpyAsync(sp.alt[a], soa[a], np * sizeof(double), kind, s->stream));
         }
         if (ids) {
-            CU(s, cudaMemcpyAsync(sp.id, ids, np * sizeof(int64_t), kind, s->stream));
+            CU(s, cudaMemcpyAsync(sp.id_alt, ids, np * sizeof(int64_t), kind, s->stream));
         } else {
             std::vector<int64_t> seq(np);
             for (int64_t i = 0; i < np; ++i) seq[i] = i;
-            CU(s, cudaMemcpyAsync(sp.id, seq.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));
+            CU(s, cudaMemcpyAsync(sp.id_alt, seq.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                  s->stream));
             CU(s, cudaStreamSynchronize(s->stream));
         }
+        CU(s, pic_launch_permute(sp.cur, sp.alt, sp.id, sp.id_alt, np, h.dim == 2 ? 1 : -1, s->stream));
         // positions to global cell units
         for (int a = 0; a < 3; ++a) {
             if (a == 1 && h.dim == 2) continue;

@@ -154,6 +154,10 @@ cudaError_t pic_launch_sort_multi(SimDev* sims, const int* slots, int nslots, in
                                   cudaStream_t st);
 cudaError_t pic_launch_finish_multi(SimDev* sims, const int* slots, int nslots, const SchedDev* sched,
                                     cudaStream_t st);
+// dst[j] = src[(j * (2^31 - 1)) mod np] for the 7 SoA arrays (array `skip`
+// left alone, -1 for none) and the ids: the one-time input-order scramble
+cudaError_t pic_launch_permute(double* const dst[7], const double* const src[7], int64_t* id_dst,
+                               const int64_t* id_src, int64_t np, int skip, cudaStream_t st);
 cudaError_t pic_launch_to_cells(double* p, int64_t np, double d, int n, cudaStream_t st);
 cudaError_t pic_launch_from_cells(const double* src, double* dst, int64_t np, double d,
                                   cudaStream_t st);

@@ -2,6 +2,8 @@
 // histogram written by the particle kernel, warp-aggregated scatter, buffer
 // swap), end-of-step bookkeeping, initial keys, per-box counts, and the
 // dispatch of the particle kernel over its two arithmetic variants.
+#include <algorithm>
+
 #include "pic_internal.h"
 #include "pic_sync.cuh"
 
@@ -243,6 +245,46 @@ cudaError_t pic_launch_finish(SimDev* dsim, const SchedDev* sched, cudaStream_t 
 cudaError_t pic_launch_box_counts(const SimDev* dsim, const SimDev& hsim, int64_t* out,
                                   cudaStream_t st) {
     pic_box_counts_kernel<<<grid_for(hsim.nboxes, 256), 256, 0, st>>>(dsim, out);
+    return cudaGetLastError();
+}
+
+// One-time scramble of a species' input order.  Within a tile the re-sort
+// keeps the relative order of the particles that stay, so an input generated
+// cell by cell would keep a warp's 32 particles in one cell for the whole run,
+// all adding to the same J entries, and the shared-memory atomics would
+// serialise.  dst[j] = src[(j * P) mod np] with P = 2^31 - 1, a prime above
+// any species size, is a bijection that spreads consecutive inputs apart.
+struct PermArrays {
+    const double* src[7];
+    double* dst[7];
+    const int64_t* id_src;
+    int64_t* id_dst;
+};
+
+__global__ void pic_permute_kernel(PermArrays A, int64_t np, int skip) {
+    const uint64_t P = 2147483647ull;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)(((uint64_t)j * P) % (uint64_t)np);
+#pragma unroll
+        for (int a = 0; a < 7; ++a)
+            if (a != skip) A.dst[a][j] = A.src[a][i];
+        A.id_dst[j] = A.id_src[i];
+    }
+}
+
+cudaError_t pic_launch_permute(double* const dst[7], const double* const src[7], int64_t* id_dst,
+                               const int64_t* id_src, int64_t np, int skip, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    PermArrays A;
+    for (int a = 0; a < 7; ++a) {
+        A.src[a] = src[a];
+        A.dst[a] = dst[a];
+    }
+    A.id_src = id_src;
+    A.id_dst = id_dst;
+    const int64_t nb = std::min<int64_t>((np + 255) / 256, 152 * 32);
+    pic_permute_kernel<<<(int)nb, 256, 0, st>>>(A, np, skip);
     return cudaGetLastError();
 }
 

@@ -142,7 +142,8 @@ def make_workload(name, scale, seed_offset=0):
         return W.uniform32(seed=1 + seed_offset)
     if name == "laser_ion_2d":
         return W.laser_ion_2d(seed=6 + seed_offset, scale=scale)
-    return W.lognormal(seed=3 + seed_offset)
+    n = max(2, 16 // scale)  # scale > 1: fewer boxes of the same recipe
+    return W.lognormal(seed=3 + seed_offset, nbox=(n, n, n))
 
 
 def workload_desc(wl):

@@ -634,6 +634,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         }
         h.tpb[a] = h.bsz[a] / h.T[a];
         h.d[a] = act ? g.dx[a] : 1.0;
+        h.invd[a] = act ? 1.0 / g.dx[a] : 0.0;
     }
     h.tiles_per_box = h.tpb[0] * h.tpb[1] * h.tpb[2];
     h.nboxes = h.nb[0] * h.nb[1] * h.nb[2];

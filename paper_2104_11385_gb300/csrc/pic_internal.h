@@ -74,6 +74,7 @@ struct SimDev {
     int jlo;              // J tile starts jlo cells below the tile origin
     double d[3];          // cell sizes
     double nd[3];         // n as doubles (periodic wrap of positions)
+    double invd[3];       // 1 / d (0 for the inactive y of 2D runs)
     double dt;
     double dtd[3];        // dt / d
     double jfac[3];       // -1/(dA_perp dt) for the prefix currents (3D); 2D see kernel

@@ -164,7 +164,17 @@ struct Arith<double> {
     __device__ static __forceinline__ double to(double x) { return x; }
     __device__ static __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
     __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
-    __device__ static __forceinline__ double two_over(double x) { return 2.0 / x; }
+    // 2/x for x >= 1: the hardware reciprocal estimate refined by two
+    // Newton-Raphson steps (e = 1 - x y, y <- y + y e; each squares the
+    // relative error), about 1 ulp, with fewer FP64 instructions than the
+    // correctly rounded division
+    __device__ static __forceinline__ double two_over(double x) {
+        double y;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+        y = ::fma(y, ::fma(-x, y, 1.0), y);
+        y = ::fma(y, ::fma(-x, y, 1.0), y);
+        return 2.0 * y;
+    }
     __device__ static __forceinline__ double c(double x) { return x; }
 };
 

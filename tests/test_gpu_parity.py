@@ -461,3 +461,43 @@ def test_energy_conserving_gather_suppresses_grid_heating():
         sim.close()
     assert drift[False] > 0.05, drift
     assert abs(drift[True]) < 1e-3, drift
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp64", "float_float"])
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_degenerate_positions_and_momenta(order, precision):
+    """Particles exactly on nodes and half nodes, at 0 and just below the
+    domain length (the integer floor paths, the periodic wrap), with momenta 0,
+    +-1e-300 (below the float range: the float-float conversions' FP64
+    route) and +-1e3 (gamma ~ 1e3), in random fields."""
+    n, box, dx = (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3)
+    rng = np.random.default_rng(500 + order)
+    L = np.array(n) * np.array(dx)
+    cells = []
+    for _ in range(300):
+        X = rng.integers(0, 16, 3).astype(np.float64)
+        kind = rng.integers(0, 4)
+        if kind == 1:
+            X += 0.5
+        elif kind == 2:
+            X[rng.integers(0, 3)] = 0.0
+        elif kind == 3:
+            X[rng.integers(0, 3)] = 16.0 - 2.0 ** -40
+        cells.append(X)
+    X = np.array(cells)
+    pos = X * np.array(dx)
+    assert (pos < L).all()
+    np_ = len(X)
+    mom = rng.choice([0.0, 1e-300, -1e-300, 1e3, -1e3, 0.3], size=(np_, 3))
+    sp = {"q": -1.0, "m": 1.0, "x": pos[:, 0].copy(), "y": pos[:, 1].copy(), "z": pos[:, 2].copy(),
+          "ux": mom[:, 0].copy(), "uy": mom[:, 1].copy(), "uz": mom[:, 2].copy(),
+          "w": np.full(np_, 1e-3), "id": np.arange(np_, dtype=np.int64)}
+    wl = {"name": "degenerate", "dim": 3, "ncell": n, "box": box, "dx": dx,
+          "dt": 0.99 * dx[0] / np.sqrt(3.0), "order": order, "absorb": 0, "species": [sp], "rho0": 0.0}
+    fields = workloads.random_fields(12, n, amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    if precision == 2:
+        sim.set_launch(precision=2)
+    sim.step(3)
+    ref.step(3)
+    compare(sim, ref, wl)

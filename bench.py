@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="foil256",
-                    choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d"])
+                    choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d", "foil_at_scale"])
     ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (debug only)")
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
@@ -142,6 +142,8 @@ def make_workload(name, scale, seed_offset=0):
         return W.uniform32(seed=1 + seed_offset)
     if name == "laser_ion_2d":
         return W.laser_ion_2d(seed=6 + seed_offset, scale=scale)
+    if name == "foil_at_scale":
+        return W.foil_at_scale(seed=5 + seed_offset)
     n = max(2, 16 // scale)  # scale > 1: fewer boxes of the same recipe
     return W.lognormal(seed=3 + seed_offset, nbox=(n, n, n))
 
@@ -538,7 +540,7 @@ def oracle_rate(wl_name, budget_s=15.0, steps=1):
     thick), timed over `steps` full PIC cycles on one host core."""
     import oracle as orc
     from paper_2104_11385_gb300 import workloads as W
-    if wl_name == "foil256":
+    if wl_name in ("foil256", "foil_at_scale"):
         wl = W.foil256(seed=2, scale=4)
         sample = "foil256 recipe at 1/4 extents: 64^3 cells, foil 2 cells thick, %d particles, %d step(s)"
     elif wl_name == "uniform32":

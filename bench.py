@@ -84,6 +84,14 @@ def _traffic_per_launch(wl, nparts):
     return c["bytes_per_particle"] * nparts
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        return float(json.load(open(MEASURED))["hbm_gbs"])
+    except Exception:
+        return HBM_FALLBACK_GBS
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -96,8 +104,8 @@ def parse():
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--precision", type=int, default=1, choices=[1, 2],
-                    help="particle push arithmetic of the main arm: 1 FP64, 2 float-float")
+    ap.add_argument("--precision", type=int, default=1, choices=[1, 2, 3],
+                    help="particle push arithmetic of the main arm: 1 FP64, 2 float-float, 3 FP32")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -282,28 +290,35 @@ def run_ours(args, rank, world):
     torch.cuda.empty_cache()
 
     # ---- the mixed-precision variant (float-float push, FP64 storage and sums)
-    mixed = None
+    mixed, fp32 = None, None
     if not args.no_mixed and args.precision == 1:
-        sim = pic.from_workload(wl, stream=stream.cuda_stream)
-        sim.set_launch(precision=2)
-        sim.step(1)
-        sim.rebalance(**dict(lbkw, theta=0.0))
-        sim.set_lb_params(**lbkw)
-        mtuned = sim.autotune(steps_per_candidate=2)
-        sim.step(args.warmup)
-        ms_mixed = timed(sim, args.steps)
-        sim.set_profiling(True)
-        sim.step(min(args.steps, 10))
-        mst = sim.stats()
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
-        mixed = {"value": nparts * args.steps * world / (ms_mixed / 1e3), "unit": "particle-updates/s",
-                 "ms_per_step": ms_mixed / args.steps,
-                 "particle_kernel_ms": mst["ms_particle"] / max(mst["steps"], 1), "launch": mtuned,
-                 "arithmetic": "float-float (FP32 pairs, ~48-bit significand) gather, Boris and deposit "
-                               "weights; FP64 storage, positions and current sums; parity 1e-10 vs the "
-                               "FP64 oracle (tests/test_gpu_parity.py)"}
+        arms = {}
+        for prec in (2, 3):
+            sim = pic.from_workload(wl, stream=stream.cuda_stream)
+            sim.set_launch(precision=prec)
+            sim.step(1)
+            sim.rebalance(**dict(lbkw, theta=0.0))
+            sim.set_lb_params(**lbkw)
+            mtuned = sim.autotune(steps_per_candidate=2)
+            sim.step(args.warmup)
+            ms_v = timed(sim, args.steps)
+            sim.set_profiling(True)
+            sim.step(min(args.steps, 10))
+            mst = sim.stats()
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
+            v = nparts * args.steps * world / (ms_v / 1e3)
+            arms[prec] = {"value": v, "unit": "particle-updates/s", "ms_per_step": ms_v / args.steps,
+                          "particle_kernel_ms": mst["ms_particle"] / max(mst["steps"], 1), "launch": mtuned,
+                          "hbm_frac": BYTES_PER_PARTICLE * nparts / (mst["ms_particle"] / max(mst["steps"], 1)
+                                                                    / 1e3) / 1e9 / hbm_peak_gbs()}
+        mixed = dict(arms[2], arithmetic="float-float (FP32 pairs, ~48-bit significand) gather, Boris and "
+                                         "deposit weights; FP64 storage, positions and current sums; parity "
+                                         "1e-10 vs the FP64 oracle (tests/test_gpu_parity.py)")
+        fp32 = dict(arms[3], arithmetic="FP32 gather, Boris and deposit weights; FP64 storage, positions "
+                                        "and current sums; parity 3e-5 (500 FP32 roundoffs) vs the FP64 "
+                                        "oracle (tests/test_gpu_parity.py)")
 
     # ---- the paper's cost strategies side by side (same schedule, same tuning)
     cost_arms = {"device_clock": nparts * args.steps * world / (ms_bal / 1e3)}
@@ -399,7 +414,7 @@ def run_ours(args, rank, world):
         "other_schedule": {"sched": other, "value": nparts * args.steps * world / (ms_other / 1e3),
                            "ms_per_step": ms_other / args.steps},
         "cost_strategies": cost_arms,
-        "mixed_precision": mixed,
+        "mixed_precision": mixed, "fp32": fp32,
         "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
         "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
                               "sort": st["ms_sort"] / max(st["steps"], 1)},
@@ -672,11 +687,12 @@ def main():
         line = {"metric": "particle-updates/s", "value": res["value"], "unit": "particle-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == 1 else "float-float",
+                "vs_baseline": None, "dtype": {1: "f64", 2: "float-float", 3: "f32"}[args.precision],
                 "data": "synthetic (seeded PCG64 workload recipe)", "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
                 "static_order": res["static_order"], "other_schedule": res["other_schedule"],
                 "cost_strategies": res["cost_strategies"], "mixed_precision": res["mixed_precision"],
+                "fp32": res["fp32"],
                 "batched_uneven_boxes": c3,
                 "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],

@@ -324,8 +324,12 @@ pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const d
  *                 2 float-float (pairs of FP32 with error-free
  *                 transformations, ~48-bit significand) for gather, Boris and
  *                 deposit weights, with FP64 storage, positions, index math and
- *                 current accumulation -- the mixed-precision variant; 0 keeps
- *                 the current setting.  The autotuner never changes it. */
+ *                 current accumulation -- the mixed-precision variant; 3 FP32
+ *                 for gather, Boris and deposit weights with FP64 storage,
+ *                 positions and current sums (the FP32 variant: about 2^-24
+ *                 per operation, so it meets an FP32-derived tolerance, not
+ *                 the FP64 one); 0 keeps the current setting.  The autotuner
+ *                 never changes it. */
 typedef struct {
     int threads, ctas_per_sm, split, precision;
 } pic_launch_cfg;

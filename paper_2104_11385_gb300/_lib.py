@@ -56,7 +56,7 @@ class LaunchCfg(ctypes.Structure):
     _fields_ = [("threads", _int), ("ctas_per_sm", _int), ("split", _int), ("precision", _int)]
 
 
-PREC_FP64, PREC_FLOAT_FLOAT = 1, 2
+PREC_FP64, PREC_FLOAT_FLOAT, PREC_FP32 = 1, 2, 3
 GATHER_MOMENTUM, GATHER_ENERGY = 0, 1
 CAPTURE_CLOCK, CAPTURE_TIME = 1, 2
 

@@ -81,7 +81,7 @@ struct pic_sim {
     int split = 16;
     int ctas = 0;
     int minb = 1;
-    int prec = 0;  // 0 FP64, 1 float-float particle push
+    int prec = 0;  // 0 FP64, 1 float-float, 2 FP32 particle push
     size_t smem = 0;
     // load balancing
     pic_lb_params lb{};
@@ -1132,7 +1132,7 @@ pic_status pic_set_launch(pic_sim* s, const pic_launch_cfg* cfg) {
     }
     const int old_split = s->split;
     if (cfg->split > 0) s->split = cfg->split;
-    if (cfg->precision < 0 || cfg->precision > 2) return fail(s, PIC_EINVAL, "precision must be 0, 1 or 2");
+    if (cfg->precision < 0 || cfg->precision > 3) return fail(s, PIC_EINVAL, "precision must be 0, 1, 2 or 3");
     if (cfg->precision > 0) {
         s->prec = cfg->precision - 1;
         s->graph_dirty = true;

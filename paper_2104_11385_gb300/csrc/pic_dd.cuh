@@ -154,6 +154,34 @@ __device__ __forceinline__ dd dd_rcp(dd x) {
     return y + y * r;
 }
 
+// ---- plain FP32 (the FP32 variant): conversions by integer work as well
+static __device__ __noinline__ float f32_from_slow(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double f64_from_slow(float f) { return (double)f; }
+
+// double -> float, rounded to 24 bits (ties away from zero on the magnitude)
+// on the bit pattern; zero, and magnitudes outside [2^-100, 2^127), take the
+// conversion instruction out of line
+__device__ __forceinline__ float f32_from(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long u = b & 0x7FFFFFFFFFFFFFFFull;
+    const int be = (int)(u >> 52);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    if (be >= 1023 - 100 && be <= 1023 + 126)
+        return __uint_as_float(sgn | (unsigned)(((u + (1ull << 28)) >> 29) - (896ull << 23)));
+    if (u == 0ull) return __uint_as_float(sgn);
+    return f32_from_slow(x);
+}
+
+// float -> double, exact: exponent rebias and mantissa << 29 for normal floats
+__device__ __forceinline__ double f64_from(float f) {
+    const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+    const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+    if (a >= 0x00800000u && a < 0x7F800000u)
+        return __longlong_as_double((long long)(sg | (((unsigned long long)a + (896ull << 23)) << 29)));
+    if (a == 0u) return __longlong_as_double((long long)sg);
+    return f64_from_slow(f);
+}
+
 // ---- one arithmetic interface for double and dd
 template <class R>
 struct Arith;
@@ -176,6 +204,16 @@ struct Arith<double> {
         return 2.0 * y;
     }
     __device__ static __forceinline__ double c(double x) { return x; }
+};
+
+template <>
+struct Arith<float> {
+    __device__ static __forceinline__ float from(double x) { return f32_from(x); }
+    __device__ static __forceinline__ double to(float x) { return f64_from(x); }
+    __device__ static __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    __device__ static __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    __device__ static __forceinline__ float two_over(float x) { return 2.0f * __frcp_rn(x); }
+    __device__ static __forceinline__ float c(double x) { return static_cast<float>(x); }
 };
 
 template <>

@@ -125,6 +125,10 @@ cudaError_t pic_prepare_particles_p0(int dim, int order, size_t smem);
 cudaError_t pic_prepare_particles_p1(int dim, int order, size_t smem);
 int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t smem);
 int pic_particle_occupancy_p1(int dim, int order, int minb, int threads, size_t smem);
+cudaError_t pic_launch_particles_p2(int dim, int order, const LaunchCfg& cfg, size_t smem,
+                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
+cudaError_t pic_prepare_particles_p2(int dim, int order, size_t smem);
+int pic_particle_occupancy_p2(int dim, int order, int minb, int threads, size_t smem);
 // self-test of the device's bounded wait: one CTA waits on an mbarrier that
 // nothing arrives at; after limit_ns it sets PIC_DERR_WAIT_TIMEOUT in *err
 cudaError_t pic_launch_selftest_wait(int32_t* err, uint64_t limit_ns, cudaStream_t st);

@@ -314,7 +314,7 @@ template <class R, int ORDER, int DIM>
 __device__ __forceinline__ void gather6(const R* __restrict__ sEB, int stride, int SX, int SY,
                                         const Support<ORDER, R>* nd, const Support<ORDER, R>* hf, R* e,
                                         R* b) {
-    if constexpr (std::is_same<R, double>::value) {
+    if constexpr (!std::is_same<R, dd>::value) {
         e[0] = interp<R, ORDER, DIM>(sEB, SX, SY, hf[0], nd[1], nd[2]);
         e[1] = interp<R, ORDER, DIM>(sEB + stride, SX, SY, nd[0], hf[1], nd[2]);
         e[2] = interp<R, ORDER, DIM>(sEB + 2 * stride, SX, SY, nd[0], nd[1], hf[2]);
@@ -459,6 +459,7 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restric
 // hence normalised) is merged first
 __device__ __forceinline__ void jadd(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jadd(double* p, dd v) { atomicAdd(p, dd_to_norm(v)); }
+__device__ __forceinline__ void jadd(double* p, float v) { atomicAdd(p, f64_from(v)); }
 
 // Esirkepov deposit of one particle into the shared J tile on windows of W
 // nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
@@ -489,7 +490,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
         Dx12[l] = k12 * wx.DS[l];
         Dz12[l] = k12 * wz.DS[l];
     }
-    if constexpr (DIM == 3 && !std::is_same<R, double>::value) {
+    if constexpr (DIM == 3 && std::is_same<R, dd>::value) {
         // float-float: one loop over the three currents (prefix axis a,
         // transverse axes b < c), to keep the code small
         R Ay[W], Dy12[W];
@@ -648,7 +649,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
     const int bx = n[0].s + lo, bz = n[2].s + lo;
-    if constexpr (DIM == 3 && !std::is_same<R, double>::value) {
+    if constexpr (DIM == 3 && std::is_same<R, dd>::value) {
         // float-float: one loop over the three currents (axis a, transverse b < c)
         const R dy = m[1].w[1] - n[1].w[1];
         const R my = fma(half, dy, n[1].w[1]);
@@ -901,7 +902,7 @@ template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
                                       const double* __restrict__ sQw, unsigned head, unsigned n,
                                       const SmemPlan& P, const R* jf, int32_t* err) {
-    if constexpr (std::is_same<R, double>::value)
+    if constexpr (!std::is_same<R, dd>::value)
         drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
     else
         drain_warp_outlined<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
@@ -915,12 +916,12 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // MINB = resident CTAs per SM the register allocation is sized for (1: up to
 // 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM).
-// PREC = arithmetic of the particle push: 0 FP64, 1 float-float (storage,
-// positions, index math and the shared J atomics stay FP64 in both).
+// PREC = arithmetic of the particle push: 0 FP64, 1 float-float, 2 FP32 (storage,
+// positions, index math and the shared J atomics stay FP64 in all three).
 template <int DIM, int ORDER, int MINB, int PREC>
 __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                               SimDev* __restrict__ sims) {
-    using R = typename std::conditional<PREC == 1, dd, double>::type;
+    using R = typename std::conditional<PREC == 1, dd, typename std::conditional<PREC == 2, float, double>::type>::type;
     using A = Arith<R>;
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -1034,6 +1035,20 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                             reinterpret_cast<dd*>(sEBd)[i] = v;
                         }
                         __syncthreads();
+                    }
+                    if constexpr (PREC == 2) {
+                        // E/B tile to FP32, compacted in place: float i lands on
+                        // bytes of double i/2 <= i, so each chunk of doubles is read
+                        // before any of its floats is written
+                        float* sEBf = reinterpret_cast<float*>(sEBd);
+                        const int ntot = 6 * P.eb_stride;
+                        for (int base = 0; base < ntot; base += blockDim.x) {
+                            const int i = base + threadIdx.x;
+                            const double v = i < ntot ? sEBd[i] : 0.0;
+                            __syncthreads();
+                            if (i < ntot) sEBf[i] = f32_from(v);
+                            __syncthreads();
+                        }
                     }
                 }
                 const unsigned long long c0 = cap_clk ? clock64() : 0ull;

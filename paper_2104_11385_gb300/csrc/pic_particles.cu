@@ -178,16 +178,19 @@ __global__ void pic_scale_copy_kernel(const double* __restrict__ s, double* __re
 // particle kernel: dispatch on the arithmetic of the push
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
                                  const SchedDev* sched, SimDev* sims, cudaStream_t st) {
+    if (cfg.prec == 2) return pic_launch_particles_p2(dim, order, cfg, smem, sched, sims, st);
     return cfg.prec == 1 ? pic_launch_particles_p1(dim, order, cfg, smem, sched, sims, st)
                          : pic_launch_particles_p0(dim, order, cfg, smem, sched, sims, st);
 }
 
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
     cudaError_t e = pic_prepare_particles_p0(dim, order, smem);
-    return e != cudaSuccess ? e : pic_prepare_particles_p1(dim, order, smem);
+    if (e == cudaSuccess) e = pic_prepare_particles_p1(dim, order, smem);
+    return e != cudaSuccess ? e : pic_prepare_particles_p2(dim, order, smem);
 }
 
 int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem, int prec) {
+    if (prec == 2) return pic_particle_occupancy_p2(dim, order, minb, threads, smem);
     return prec == 1 ? pic_particle_occupancy_p1(dim, order, minb, threads, smem)
                      : pic_particle_occupancy_p0(dim, order, minb, threads, smem);
 }

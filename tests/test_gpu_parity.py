@@ -501,3 +501,43 @@ def test_degenerate_positions_and_momenta(order, precision):
     sim.step(3)
     ref.step(3)
     compare(sim, ref, wl)
+
+
+# FP32 variant: every gather, Boris and deposit-weight operation rounds to 2^-24
+# (u ~ 6e-8).  A step chains about 30 of them on a particle (u^{n+1/2} ~ 10 u
+# relative), currents inherit the weights' error, and 10 steps accumulate
+# ~100 u; fields of a quiet plasma are themselves sums of such currents.
+# Tolerance 500 u = 3e-5 (measured worst 6e-6, on the thermal 32^3 plasma).
+TOL_FP32 = 3e-5
+
+
+@pytest.mark.parametrize("case", FF_CASES, ids=[f"{c[0]}d_o{c[4]}" for c in FF_CASES])
+def test_fp32_variant_parity(case):
+    """FP32 push (FP64 storage, positions and current sums) against the FP64
+    oracle after 10 steps, at the FP32-derived tolerance."""
+    dim, n, box, dx, order = case
+    wl = workloads.random_plasma(500 + sum(n) + order, dim, n, box, dx, order, nspecies=2, npart=4000,
+                                 umax=2.0)
+    fields = workloads.random_fields(8, n, amp=0.2)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    sim.set_launch(precision=3)
+    assert sim.get_launch()["precision"] == 3
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl, tol=TOL_FP32)
+
+
+def test_fp32_variant_uniform32_and_laser():
+    wl = workloads.uniform32()
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(precision=3)
+    sim.step(10)
+    ref.step(10)
+    compare(sim, ref, wl, tol=TOL_FP32)
+    wl = workloads.random_plasma(77, 3, (16, 16, 48), (8, 8, 16), (0.3, 0.3, 0.3), 1, nspecies=2, npart=3000,
+                                 umax=3.0, absorb=6, laser=True)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(precision=3)
+    sim.step(12)
+    ref.step(12)
+    compare(sim, ref, wl, tol=TOL_FP32)

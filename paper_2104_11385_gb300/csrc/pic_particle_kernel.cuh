@@ -1038,15 +1038,25 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     }
                     if constexpr (PREC == 2) {
                         // E/B tile to FP32, compacted in place: float i lands on
-                        // bytes of double i/2 <= i, so each chunk of doubles is read
-                        // before any of its floats is written
+                        // bytes of double i/2 <= i, so each round reads its 4 x
+                        // blockDim doubles before any of its floats is written
+                        // (a round's floats cover doubles below its own end)
                         float* sEBf = reinterpret_cast<float*>(sEBd);
                         const int ntot = 6 * P.eb_stride;
-                        for (int base = 0; base < ntot; base += blockDim.x) {
-                            const int i = base + threadIdx.x;
-                            const double v = i < ntot ? sEBd[i] : 0.0;
+                        constexpr int K = 4;
+                        for (int base = 0; base < ntot; base += K * blockDim.x) {
+                            double v[K];
+#pragma unroll
+                            for (int q = 0; q < K; ++q) {
+                                const int i = base + q * blockDim.x + threadIdx.x;
+                                v[q] = i < ntot ? sEBd[i] : 0.0;
+                            }
                             __syncthreads();
-                            if (i < ntot) sEBf[i] = f32_from(v);
+#pragma unroll
+                            for (int q = 0; q < K; ++q) {
+                                const int i = base + q * blockDim.x + threadIdx.x;
+                                if (i < ntot) sEBf[i] = f32_from(v[q]);
+                            }
                             __syncthreads();
                         }
                     }

@@ -37,8 +37,8 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # algorithmic FP64 flops per particle update, in-cell path (3D linear: gather 126,
 # local positions and half-node shifts 6, Boris push 70, Esirkepov deposit 73, positions 3)
-FLOPS_PER_PARTICLE = {(3, 1): 278.0, (3, 2): 766.0, (3, 3): 1594.0, (2, 1): 170.0, (2, 2): 350.0,
-                      (2, 3): 548.0}
+FLOPS_PER_PARTICLE = {(3, 1): 275.0, (3, 2): 763.0, (3, 3): 1591.0, (2, 1): 168.0, (2, 2): 348.0,
+                      (2, 3): 546.0}
 BYTES_PER_PARTICLE = 104.0  # read x,y,z,ux,uy,uz,w (56) + write x..uz (48)
 BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 

@@ -438,13 +438,17 @@ __host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3])
     return p;
 }
 
-template <int DIM, int ORDER>
-__device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restrict__ sJ,
+template <int DIM, int ORDER, class JT>
+__device__ void flush_j(const SimDev& S, const Tile& tl, const JT* __restrict__ sJ,
                         const SmemPlan& P) {
     const int jx = S.js[0], jy = S.js[1];
     for (int idx = threadIdx.x; idx < 3 * P.j_vol; idx += blockDim.x) {
         int comp = idx / P.j_vol, r = idx - comp * P.j_vol;
-        double v = sJ[comp * P.j_stride + r];
+        double v;
+        if constexpr (std::is_same<JT, float>::value)
+            v = f64_from(sJ[comp * P.j_stride + r]);
+        else
+            v = sJ[comp * P.j_stride + r];
         if (v == 0.0) continue;
         int a = r % jx, b = (r / jx) % jy, c = r / (jx * jy);
         int gx = modi(tl.o[0] - S.jlo + a, S.n[0]);
@@ -460,6 +464,19 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const double* __restric
 __device__ __forceinline__ void jadd(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jadd(double* p, dd v) { atomicAdd(p, dd_to_norm(v)); }
 __device__ __forceinline__ void jadd(double* p, float v) { atomicAdd(p, f64_from(v)); }
+__device__ __forceinline__ void jadd(float* p, float v) { atomicAdd(p, v); }
+
+// element type of the shared J tile: FP32 for the FP32 variant (its own
+// tolerance covers the FP32 sums, and no FP64 compare-and-swap runs), FP64
+// otherwise; the flush adds each entry to the global FP64 J
+template <class R>
+struct JAcc {
+    using type = double;
+};
+template <>
+struct JAcc<float> {
+    using type = float;
+};
 
 // Esirkepov deposit of one particle into the shared J tile on windows of W
 // nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
@@ -467,7 +484,8 @@ __device__ __forceinline__ void jadd(double* p, float v) { atomicAdd(p, f64_from
 // weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3 = A_a A_b + DS_a DS_b / 12
 // with A = S0 + DS/2.  qw and vy in R; the prefactors -1/(dA dt) come from jf.
 template <class R, int DIM, int ORDER, int W>
-__device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ, const SmemPlan& P,
+__device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type* __restrict__ sJ,
+                                        const SmemPlan& P,
                                         R qw, R vy, const R* jf, const Support<ORDER, R>& n0,
                                         const Support<ORDER, R>& n1, const Support<ORDER, R>& n2,
                                         const Support<ORDER, R>& m0, const Support<ORDER, R>& m1,
@@ -478,9 +496,10 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
     if (DIM == 3) ok = ok && make_window<ORDER, W, R>(n1, m1, wy);
     if (!ok) return false;
     const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
-    double* Jx = sJ;
-    double* Jy = sJ + P.j_stride;
-    double* Jz = sJ + 2 * P.j_stride;
+    using JT = typename JAcc<R>::type;
+    JT* Jx = sJ;
+    JT* Jy = sJ + P.j_stride;
+    JT* Jz = sJ + 2 * P.j_stride;
     const R half = A::c(0.5), k12 = A::c(1.0 / 12.0);
     R Ax[W], Az[W], Dx12[W], Dz12[W];
 #pragma unroll
@@ -500,7 +519,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             Dy12[l] = k12 * wy.DS[l];
         }
         const int sxy = jx * jy;
-        double* origin = sJ + ((wz.base + lo) * jy + (wy.base + lo)) * jx + (wx.base + lo);
+        JT* origin = sJ + ((wz.base + lo) * jy + (wy.base + lo)) * jx + (wx.base + lo);
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -519,7 +538,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
                 Ac[l] = c == 1 ? Ay[l] : Az[l];
                 Dc12[l] = c == 1 ? Dy12[l] : Dz12[l];
             }
-            double* Ja = origin + a * P.j_stride;
+            JT* Ja = origin + a * P.j_stride;
 #pragma unroll 1
             for (int k = 0; k < W; ++k) {
                 R ack = Ac[0], dck = Dc12[0];
@@ -531,7 +550,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const R T = fma(Ab[j], ack, Db[j] * dck);
-                    double* row = Ja + k * sc + j * sb;
+                    JT* row = Ja + k * sc + j * sb;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) jadd(row + l * sa, Pf[l] * T);
                 }
@@ -553,7 +572,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const R T = fma(Ay[j], Az[k], wy.DS[j] * Dz12[k]);
-                    double* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
+                    JT* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * T);
                 }
@@ -569,7 +588,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Az[k], wx.DS[i] * Dz12[k]);
-                    double* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
+                    JT* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
 #pragma unroll
                     for (int j = 0; j < W - 1; ++j) jadd(col + j * jx, Pf[j] * T);
                 }
@@ -585,7 +604,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Ay[j], Dx12[i] * wy.DS[j]);
-                    double* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
+                    JT* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
 #pragma unroll
                     for (int k = 0; k < W - 1; ++k) jadd(col + k * jx * jy, Pf[k] * T);
                 }
@@ -600,7 +619,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             for (int l = 0; l < W - 1; ++l) { acc = acc + wx.DS[l]; Pf[l] = c * acc; }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                double* row = Jx + (bz + k) * jx + bx;
+                JT* row = Jx + (bz + k) * jx + bx;
 #pragma unroll
                 for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * Az[k]);
             }
@@ -613,7 +632,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
             for (int k = 0; k < W - 1; ++k) { acc = acc + wz.DS[k]; Pf[k] = c * acc; }
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                double* col = Jz + bz * jx + (bx + i);
+                JT* col = Jz + bz * jx + (bx + i);
 #pragma unroll
                 for (int k = 0; k < W - 1; ++k) jadd(col + k * jx, Pf[k] * Ax[i]);
             }
@@ -636,15 +655,16 @@ __device__ __forceinline__ bool deposit(const SimDev& S, double* __restrict__ sJ
 // A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
 // deposit<R, DIM, 1, 2>, with fewer instructions.
 template <class R, int DIM>
-__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __restrict__ sJ,
+__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, typename JAcc<R>::type* __restrict__ sJ,
                                                    const SmemPlan& P, R qw, R vy, const R* jf,
                                                    const Support<1, R>* n, const Support<1, R>* m) {
     using A = Arith<R>;
     const R k12 = A::c(1.0 / 12.0), half = A::c(0.5), one = A::c(1.0);
     const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
-    double* Jx = sJ;
-    double* Jy = sJ + P.j_stride;
-    double* Jz = sJ + 2 * P.j_stride;
+    using JT = typename JAcc<R>::type;
+    JT* Jx = sJ;
+    JT* Jy = sJ + P.j_stride;
+    JT* Jz = sJ + 2 * P.j_stride;
     const R dx = m[0].w[1] - n[0].w[1], dz = m[2].w[1] - n[2].w[1];
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
@@ -656,7 +676,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
         const R ay0 = one - my;
         const int by = n[1].s + lo;
         const int sxy = jx * jy;
-        double* origin = sJ + (bz * jy + by) * jx + bx;
+        JT* origin = sJ + (bz * jy + by) * jx + bx;
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -666,7 +686,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
             const R ab = b == 0 ? ax0 : ay0, ac = c == 1 ? ay0 : az0;
             const R e = (db * dc) * k12;
             const R pf = -((qw * pick3(a, jf[0], jf[1], jf[2])) * pick3(a, dx, dy, dz));
-            double* r = origin + a * P.j_stride;
+            JT* r = origin + a * P.j_stride;
             jadd(r, pf * fma(ab, ac, e));
             jadd(r + sb, pf * fma(mb, ac, -e));
             jadd(r + sc, pf * fma(ab, mc, -e));
@@ -680,7 +700,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
         {   // Jx at (bx, by + j, bz + k)
             const R e = (dy * dz) * k12;
             const R pf = -((qw * jf[0]) * dx);
-            double* r = Jx + (bz * jy + by) * jx + bx;
+            JT* r = Jx + (bz * jy + by) * jx + bx;
             jadd(r, pf * fma(ay0, az0, e));
             jadd(r + jx, pf * fma(my, az0, -e));
             jadd(r + jx * jy, pf * fma(ay0, mz, -e));
@@ -689,7 +709,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
         {   // Jy at (bx + i, by, bz + k)
             const R e = (dx * dz) * k12;
             const R pf = -((qw * jf[1]) * dy);
-            double* r = Jy + (bz * jy + by) * jx + bx;
+            JT* r = Jy + (bz * jy + by) * jx + bx;
             jadd(r, pf * fma(ax0, az0, e));
             jadd(r + 1, pf * fma(mx, az0, -e));
             jadd(r + jx * jy, pf * fma(ax0, mz, -e));
@@ -698,7 +718,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
         {   // Jz at (bx + i, by + j, bz)
             const R e = (dx * dy) * k12;
             const R pf = -((qw * jf[2]) * dz);
-            double* r = Jz + (bz * jy + by) * jx + bx;
+            JT* r = Jz + (bz * jy + by) * jx + bx;
             jadd(r, pf * fma(ax0, ay0, e));
             jadd(r + 1, pf * fma(mx, ay0, -e));
             jadd(r + jx, pf * fma(ax0, my, -e));
@@ -707,20 +727,20 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
     } else {
         {   // Jx at (bx, bz + k): -(q w/(dz dt)) DSx A_z
             const R pf = -((qw * jf[0]) * dx);
-            double* r = Jx + bz * jx + bx;
+            JT* r = Jx + bz * jx + bx;
             jadd(r, pf * az0);
             jadd(r + jx, pf * mz);
         }
         {   // Jz at (bx + i, bz)
             const R pf = -((qw * jf[2]) * dz);
-            double* r = Jz + bz * jx + bx;
+            JT* r = Jz + bz * jx + bx;
             jadd(r, pf * ax0);
             jadd(r + 1, pf * mx);
         }
         {   // out-of-plane Jy at (bx + i, bz + k)
             const R e = (dx * dz) * k12;
             const R c = qw * vy * jf[1];
-            double* r = Jy + bz * jx + bx;
+            JT* r = Jy + bz * jx + bx;
             jadd(r, c * fma(ax0, az0, e));
             jadd(r + 1, c * fma(mx, az0, -e));
             jadd(r + jx, c * fma(ax0, mz, -e));
@@ -734,7 +754,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, double* __re
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
 template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
-                                         const R* __restrict__ sEB, double* __restrict__ sJ,
+                                         const R* __restrict__ sEB, typename JAcc<R>::type* __restrict__ sJ,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                          const R* jf, const R* dtd, R kq, R qs, int64_t p, int32_t* err) {
     using A = Arith<R>;
@@ -859,7 +879,7 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
 // A warp deposits n <= 32 queued (cell-crossing) particles of its ring,
 // starting at slot head, on the ORDER + 2 window: lane i takes entry head + i.
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
+__device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, typename JAcc<R>::type* __restrict__ sJ,
                                            const double* __restrict__ sQw, unsigned head, unsigned n,
                                            const SmemPlan& P, const R* jf, int32_t* err) {
     using A = Arith<R>;
@@ -892,14 +912,15 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, doub
 // and rare, and inlined into the particle loop it crowds the instruction cache
 // (about 5 % of the kernel); FP64 is indifferent and inlines it
 template <class R, int DIM, int ORDER>
-__device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
+__device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl,
+                                                 typename JAcc<R>::type* __restrict__ sJ,
                                                  const double* __restrict__ sQw, unsigned head, unsigned n,
                                                  const SmemPlan& P, const R* jf, int32_t* err) {
     drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
 }
 
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, double* __restrict__ sJ,
+__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, typename JAcc<R>::type* __restrict__ sJ,
                                       const double* __restrict__ sQw, unsigned head, unsigned n,
                                       const SmemPlan& P, const R* jf, int32_t* err) {
     if constexpr (!std::is_same<R, dd>::value)
@@ -973,7 +994,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         const SmemPlan P = smem_plan(S.ebs, S.js);
         double* sEBd = smem;
         const R* sEB = reinterpret_cast<const R*>(smem);
-        double* sJ = smem + 6 * P.eb_stride;
+        double* sJd = smem + 6 * P.eb_stride;  // J region (doubles); the queues follow it
+        using JT = typename JAcc<R>::type;
+        JT* sJ = reinterpret_cast<JT*>(sJd);
         unsigned long long my_clk = 0ull;
         // the simulation's constants in R
         const R jf[3] = {A::from(S.jfac[0]), A::from(DIM == 3 ? S.jfac[1] : S.jyfac2d), A::from(S.jfac[2])};
@@ -997,7 +1020,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     if (cur.t >= 0) {
                         const SimDev& CS = sims[cur.sim];
                         const SmemPlan CP = smem_plan(CS.ebs, CS.js);
-                        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+                        flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const typename JAcc<R>::type*>(smem + 6 * CP.eb_stride), CP);
                         __syncthreads();
                     }
                     cur.sim = unit.sim;
@@ -1014,7 +1037,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         for (int c = 0; c < 6; ++c)
                             tma_load_3d(sEBd + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
                     }
-                    for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJ[i] = 0.0;
+                    for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJd[i] = 0.0;
                     bool ok = mbar_wait_bounded(&bar, phase);
                     phase ^= 1u;
                     if (!ok) {
@@ -1065,7 +1088,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 {
                     // per-warp loop: no CTA barrier until the tile changes
                     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                    double* sQw = sJ + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
+                    double* sQw = sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
                     volatile unsigned* vtail = s_qtail + warp;
                     for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
                         const int64_t p = p0 + lane;
@@ -1112,7 +1135,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         __syncthreads();
         const SimDev& CS = sims[cur.sim];
         const SmemPlan CP = smem_plan(CS.ebs, CS.js);
-        flush_j<DIM, ORDER>(CS, cur, smem + 6 * CP.eb_stride, CP);
+        flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const typename JAcc<R>::type*>(smem + 6 * CP.eb_stride), CP);
     }
 }
 

@@ -106,7 +106,7 @@ __device__ __forceinline__ bool ge_half(double f) {  // f >= 0.5 for f >= 0
 }
 
 // one-dimensional B-spline support: first node and ORDER+1 weights in the
-// arithmetic type R (double, or dd for the float-float variant)
+// arithmetic type R (double; dd for the float-float variant; float for the FP32 one)
 template <int ORDER, class R>
 struct Support {
     int s;
@@ -306,8 +306,8 @@ __device__ __forceinline__ T pick3(int a, const T& v0, const T& v1, const T& v2)
 }
 
 // The six E/B components at one particle.  E_a sits on the half-node grid
-// along a and on nodes across it, B_a the other way round.  FP64 unrolls the
-// six interpolations; float-float runs them as a loop (its operations are
+// along a and on nodes across it, B_a the other way round.  FP64 and FP32
+// unroll the six interpolations; float-float runs them as a loop (its operations are
 // 7-11 FP32 instructions each, and six unrolled copies overflow the
 // instruction cache).
 template <class R, int ORDER, int DIM>
@@ -459,8 +459,8 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const JT* __restrict__ 
 }
 
 
-// shared-memory J atomics take doubles; a float-float value (a product,
-// hence normalised) is merged first
+// shared-memory J atomics: doubles for FP64 and float-float (a float-float
+// value is renormalised and merged to one double first), floats for FP32
 __device__ __forceinline__ void jadd(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void jadd(double* p, dd v) { atomicAdd(p, dd_to_norm(v)); }
 __device__ __forceinline__ void jadd(double* p, float v) { atomicAdd(p, f64_from(v)); }
@@ -910,7 +910,7 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, type
 
 // float-float keeps the drain out of line: the cell-crossing deposit is long
 // and rare, and inlined into the particle loop it crowds the instruction cache
-// (about 5 % of the kernel); FP64 is indifferent and inlines it
+// (about 5 % of the kernel); FP64 is indifferent and inlines it, as does FP32
 template <class R, int DIM, int ORDER>
 __device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl,
                                                  typename JAcc<R>::type* __restrict__ sJ,

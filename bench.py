@@ -100,7 +100,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="foil256",
                     choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d", "foil_at_scale"])
-    ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (debug only)")
+    ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (small cases for profiling)")
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
     ap.add_argument("--threads", type=int, default=0)

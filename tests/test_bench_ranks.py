@@ -42,3 +42,24 @@ def test_max_over_ranks_two_gloo_ranks():
 def test_max_over_ranks_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the FP64 CPU oracle on a bounded sample
+    and prints one JSON line with the contract's keys (CPU only)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--workload", "uniform32"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "particle-updates/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    for k in ("unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config"):
+        assert k in d

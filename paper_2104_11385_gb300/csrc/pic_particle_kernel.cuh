@@ -96,6 +96,11 @@ __device__ __forceinline__ int ifloor(double x) {
     return ifloor_slow(x);
 }
 
+// periodic image of a position that left [0, n) by less than n: a separate
+// function, so that the rare FP64 add is a branch and not a predicated
+// instruction holding the FP64 pipe for every particle
+static __device__ __noinline__ double wrap_periodic(double x, double n) { return x < 0.0 ? x + n : x - n; }
+
 // x < 0 and x >= y for y > 0 by integer comparison of the bit patterns
 __device__ __forceinline__ bool is_neg(double x) { return __double_as_longlong(x) < 0; }
 __device__ __forceinline__ bool ge_pos(double x, double y) {
@@ -844,12 +849,10 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     // ---- new position, boundary, re-sort key
     X = X1;
     Z = Z1;
-    if (is_neg(X)) X += S.nd[0];
-    if (ge_pos(X, S.nd[0])) X -= S.nd[0];
+    if (is_neg(X) || ge_pos(X, S.nd[0])) X = wrap_periodic(X, S.nd[0]);
     if (DIM == 3) {
         Y = Y1;
-        if (is_neg(Y)) Y += S.nd[1];
-        if (ge_pos(Y, S.nd[1])) Y -= S.nd[1];
+        if (is_neg(Y) || ge_pos(Y, S.nd[1])) Y = wrap_periodic(Y, S.nd[1]);
     }
     int key = -1;
     if (S.absorb > 0) {
@@ -857,8 +860,7 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         const int iz = ifloor(Z);
         if (iz < S.absorb || iz >= S.n[2] - S.absorb) key = S.ntiles;
     } else {
-        if (is_neg(Z)) Z += S.nd[2];
-        if (ge_pos(Z, S.nd[2])) Z -= S.nd[2];
+        if (is_neg(Z) || ge_pos(Z, S.nd[2])) Z = wrap_periodic(Z, S.nd[2]);
     }
     if (key < 0) {
         int ix = min(max(ifloor(X), 0), S.n[0] - 1);

@@ -130,6 +130,21 @@ pic_status fail(pic_sim* s, pic_status st, const char* fmt, ...) {
             return fail((s), PIC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
+// a temporary device buffer for one call: a failed allocation is PIC_ENOMEM
+// (the handle stays usable), not a device error
+template <class T>
+pic_status talloc(pic_sim* s, T** p, size_t n) {
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(s, PIC_ENOMEM, "temporary cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    *p = (T*)q;
+    return PIC_OK;
+}
+
 template <class T>
 pic_status dalloc(pic_sim* s, T** p, size_t n) {
     void* q = nullptr;
@@ -834,7 +849,7 @@ pic_status pic_set_field(pic_sim* s, int comp, const double* data, int on_device
     const double* src = data;
     double* tmp = nullptr;
     if (!on_device) {
-        CU(s, cudaMalloc(&tmp, nc * sizeof(double)));
+        TRY(talloc(s, &tmp, (size_t)nc));
         CU(s, cudaMemcpyAsync(tmp, data, nc * sizeof(double), cudaMemcpyHostToDevice, s->stream));
         src = tmp;
     }
@@ -1057,7 +1072,7 @@ pic_status pic_read_fields(pic_sim* s, int comp, double* out, int on_device) {
     double* dst = out;
     double* tmp = nullptr;
     if (!on_device) {
-        CU(s, cudaMalloc(&tmp, nc * sizeof(double)));
+        TRY(talloc(s, &tmp, (size_t)nc));
         dst = tmp;
     }
     cudaError_t e;
@@ -1092,7 +1107,7 @@ pic_status pic_read_particles(pic_sim* s, int species, double* const soa_out[7],
     const SpeciesDev& sp = s->h.sp[species];
     if (np == 0) return PIC_OK;
     double* tmp = nullptr;
-    if (!on_device) CU(s, cudaMalloc(&tmp, np * sizeof(double)));
+    if (!on_device) TRY(talloc(s, &tmp, (size_t)np));
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 7 && e == cudaSuccess; ++a) {
         if (!soa_out[a]) continue;

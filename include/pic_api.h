@@ -41,7 +41,7 @@ typedef enum {
     PIC_ECUDA = -3,        /* a CUDA call failed (handle is then poisoned)      */
     PIC_ETIMEOUT = -4,     /* a bounded device-side wait ran out (poisoned)     */
     PIC_ESTATE = -5,       /* handle poisoned, or call made in the wrong state  */
-    PIC_EUNSUPPORTED = -6  /* valid request that this build does not support   */
+    PIC_EUNSUPPORTED = -6  /* valid request that libpic does not support       */
 } pic_status;
 
 typedef struct pic_sim pic_sim; /* opaque, library-owned */

@@ -1,12 +1,13 @@
 // pic_particle_kernel.cuh -- the particle side of the PIC cycle on sm_103a,
 // templated on the arithmetic of the particle push (included by one
-// translation unit per precision: pic_particles_f64.cu, pic_particles_dd.cu).
+// translation unit per precision: pic_particles_f64.cu, pic_particles_dd.cu,
+// pic_particles_f32.cu).
 //
 // pic_particle_kernel: persistent CTAs pull work units (a chunk of one box's
 // particles) from cost-ordered lists.  For every tile (sub-box) a unit touches,
 // the guard-extended E/B tile is staged into shared memory by TMA
 // (cp.async.bulk.tensor, local HBM only, no multicast), the current is
-// deposited into a shared-memory J tile with shared FP64 atomics and flushed
+// deposited into a shared-memory J tile with shared atomics and flushed
 // once per tile into the global J arrays.  Each thread brackets its particle
 // loop with clock64(); the deltas are warp-reduced, summed in shared memory and
 // added once per unit to the box's cost -- the device-clock cost of
@@ -866,7 +867,10 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
         int ix = min(max(ifloor(X), 0), S.n[0] - 1);
         int iy = (DIM == 3) ? min(max(ifloor(Y), 0), S.n[1] - 1) : 0;
         int iz = min(max(ifloor(Z), 0), S.n[2] - 1);
-        key = tile_key(S, ix, iy, iz);
+        // most particles stay in their tile: its key without the divisions
+        bool own = (unsigned)(ix - tl.o[0]) < (unsigned)S.T[0] && (unsigned)(iz - tl.o[2]) < (unsigned)S.T[2];
+        if (DIM == 3) own = own && (unsigned)(iy - tl.o[1]) < (unsigned)S.T[1];
+        key = own ? tl.t : tile_key(S, ix, iy, iz);
     }
     sp.cur[0][p] = X;
     if (DIM == 3) sp.cur[1][p] = Y;
@@ -940,7 +944,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // MINB = resident CTAs per SM the register allocation is sized for (1: up to
 // 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM).
 // PREC = arithmetic of the particle push: 0 FP64, 1 float-float, 2 FP32 (storage,
-// positions, index math and the shared J atomics stay FP64 in all three).
+// positions and index math stay FP64 in all three; the shared J tile is FP64
+// except in the FP32 variant, whose tile sums in FP32).
 template <int DIM, int ORDER, int MINB, int PREC>
 __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                               SimDev* __restrict__ sims) {

@@ -82,7 +82,8 @@ enum {
     PIC_REQ_PENDING = 0, /* waiting for a slot and memory   */
     PIC_REQ_ACTIVE = 1,  /* resident, stepping every tick    */
     PIC_REQ_DONE = 2,    /* finished, results resident       */
-    PIC_REQ_RELEASED = 3
+    PIC_REQ_RELEASED = 3,
+    PIC_REQ_CANCELLED = 4 /* withdrawn by pic_server_cancel */
 };
 
 pic_status pic_server_create(const pic_server_desc* desc, pic_server** out);
@@ -113,6 +114,17 @@ pic_status pic_server_read_particles(pic_server* srv, int64_t req_id, int specie
 
 /* Frees a DONE request's device state (its footprint leaves the budget). */
 pic_status pic_server_release(pic_server* srv, int64_t req_id);
+
+/* Withdraws a request that has not finished, between ticks: a PENDING one
+ * leaves the queue without being admitted; an ACTIVE one stops stepping, its
+ * device state is freed, and its slot and footprint go back to the server, so
+ * the next tick can admit the next pending request into them.  The other
+ * requests are unaffected (their state lives in their own slots).  The state
+ * becomes PIC_REQ_CANCELLED and the request has no results.  Synchronises the
+ * server's stream first.  Errors: PIC_EINVAL (unknown id), PIC_ESTATE (the
+ * request is DONE, RELEASED or already CANCELLED: use pic_server_release for a
+ * finished one). */
+pic_status pic_server_cancel(pic_server* srv, int64_t req_id);
 
 /* Device bytes of a request as admitted (or as estimated while pending). */
 pic_status pic_server_footprint(pic_server* srv, int64_t req_id, int64_t* bytes);

@@ -90,7 +90,7 @@ class ServerStats(ctypes.Structure):
                 ("admitted", _i64), ("finished", _i64), ("bytes_in_use", _i64)]
 
 
-REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED = range(4)
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED, REQ_CANCELLED = range(5)
 
 # (name, restype, argtypes) of every exported function of include/*.h
 SIGNATURES = [
@@ -132,6 +132,7 @@ SIGNATURES = [
     ("pic_server_num_particles", _int, [_vp, _i64, _int, _pi64]),
     ("pic_server_read_particles", _int, [_vp, _i64, _int, ctypes.POINTER(_vp), _vp]),
     ("pic_server_release", _int, [_vp, _i64]),
+    ("pic_server_cancel", _int, [_vp, _i64]),
     ("pic_server_footprint", _int, [_vp, _i64, _pi64]),
     ("pic_server_get_stats", _int, [_vp, ctypes.POINTER(ServerStats)]),
     ("pic_server_destroy", _int, [_vp]),

@@ -502,6 +502,32 @@ pic_status pic_server_release(pic_server* s, int64_t id) {
     return PIC_OK;
 }
 
+pic_status pic_server_cancel(pic_server* s, int64_t id) {
+    if (!s) return PIC_EINVAL;
+    Request* r = find(s, id);
+    if (!r) return sfail(s, PIC_EINVAL, "unknown request");
+    if (r->state == PIC_REQ_PENDING) {
+        s->pending.erase(std::find(s->pending.begin(), s->pending.end(), id));
+        r->arrays.clear();
+        r->ids.clear();
+    } else if (r->state == PIC_REQ_ACTIVE) {
+        // no device work of the server is in flight after this: the slot's
+        // entry in the packed launch is dropped when the next tick rebuilds
+        // its work units (before it launches anything)
+        SCU(s, cudaStreamSynchronize(s->stream));
+        s->slot_owner[r->slot] = -1;
+        r->slot = -1;
+        pic_destroy(r->sim);
+        r->sim = nullptr;
+        s->bytes_in_use -= r->footprint;
+        s->dirty = true;
+    } else {
+        return sfail(s, PIC_ESTATE, "request is finished, released or cancelled");
+    }
+    r->state = PIC_REQ_CANCELLED;
+    return PIC_OK;
+}
+
 pic_status pic_server_footprint(pic_server* s, int64_t id, int64_t* bytes) {
     if (!s || !bytes) return PIC_EINVAL;
     Request* r = find(s, id);

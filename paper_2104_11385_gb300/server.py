@@ -106,6 +106,10 @@ class Server:
     def release(self, rid):
         self._check(self._lib.pic_server_release(self._h, int(rid)))
 
+    def cancel(self, rid):
+        """Withdraws a pending or active request between ticks (pic_server_cancel)."""
+        self._check(self._lib.pic_server_cancel(self._h, int(rid)))
+
     def footprint(self, rid) -> int:
         b = ctypes.c_int64()
         self._check(self._lib.pic_server_footprint(self._h, int(rid), ctypes.byref(b)))

@@ -133,3 +133,50 @@ def test_langmuir_ripple_oscillates_at_plasma_frequency():
     e2 = srv.read_field(r2, L.EX, n).mean(axis=(0, 1))
     c = float(np.dot(e1, e2) / np.sqrt(np.dot(e1, e1) * np.dot(e2, e2)))
     assert c < -0.8, c
+
+
+def test_cancel_pending_and_active_requests():
+    """A withdrawn request leaves between ticks: a pending one is never
+    admitted, an active one frees its slot and memory for the next pending
+    request, and a request still running finishes with its result alone."""
+    alone = Server(dim=2, max_active=8)
+    ra = alone.submit(**A)
+    _run_one(alone, ra)
+    ref = _result(alone, ra, A["ncell"])
+    alone.close()
+
+    srv = Server(dim=2, max_active=2)
+    busy = srv.submit((128, 1, 128), (32, 1, 32), (0.2, 1, 0.2), 500, plasma=dict(ppc=8, seed=3))
+    rb = srv.submit(**A)
+    waiting = srv.submit((64, 1, 64), (32, 1, 32), (0.2, 1, 0.2), 20, plasma=dict(ppc=2, seed=6))
+    dropped = srv.submit((64, 1, 64), (32, 1, 32), (0.2, 1, 0.2), 20, plasma=dict(ppc=2, seed=7))
+    for _ in range(5):
+        srv.tick()
+    assert srv.poll(busy)["state"] == L.REQ_ACTIVE and srv.poll(waiting)["state"] == L.REQ_PENDING
+    held = srv.stats()["bytes_in_use"]
+    srv.cancel(dropped)
+    srv.cancel(busy)
+    assert srv.stats()["bytes_in_use"] == held - srv.footprint(busy)
+    assert srv.poll(busy)["state"] == L.REQ_CANCELLED and srv.poll(busy)["steps"] == 5
+    srv.tick()
+    assert srv.poll(waiting)["state"] == L.REQ_ACTIVE  # took the freed slot
+    srv.run_until_idle()
+    assert srv.poll(dropped)["state"] == L.REQ_CANCELLED and srv.poll(dropped)["t_admit"] < 0
+    assert srv.poll(waiting)["state"] == L.REQ_DONE and srv.stats()["finished"] == 2
+    got = _result(srv, rb, A["ncell"])
+    for fg, fr in zip(got[0], ref[0]):
+        assert rel(fg, fr) < TOL
+    for k in ("x", "z", "ux", "uy", "uz"):
+        assert rel(got[1][k], ref[1][k]) < TOL
+    assert np.array_equal(got[1]["id"], ref[1]["id"])
+    # a cancelled request has no results; finished or cancelled ones cannot be cancelled
+    with pytest.raises(L.PicError) as ei:
+        srv.read_field(busy, L.EX, (128, 1, 128))
+    assert ei.value.status == L.PIC_ESTATE
+    for rid in (busy, rb):
+        with pytest.raises(L.PicError) as ei:
+            srv.cancel(rid)
+        assert ei.value.status == L.PIC_ESTATE
+    with pytest.raises(L.PicError) as ei:
+        srv.cancel(10_000)
+    assert ei.value.status == L.PIC_EINVAL

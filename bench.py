@@ -603,7 +603,9 @@ def run_timeline(args):
     the same workload, launch and schedule under no balancing (the fixed
     equal-count Morton mapping), static balancing (once, at the first
     interval) and dynamic balancing (every interval, threshold theta), with
-    the time per step and E (Eq. 1) of the mapping in force every interval."""
+    the time per step and E (Eq. 1) of the mapping in force every interval.
+    Dynamic balancing runs with both of the paper's policies: knapsack and
+    the Morton space-filling curve."""
     import torch
     import paper_2104_11385_gb300 as pic
     wl = make_workload(args.workload, args.scale)
@@ -612,9 +614,12 @@ def run_timeline(args):
     sched = pic.SCHED_LISTS if args.sched == "lists" else pic.SCHED_QUEUE
     stream = torch.cuda.Stream()
     out = {}
-    for name, mode in (("none", pic.LB_NONE), ("static", pic.LB_STATIC), ("dynamic", pic.LB_DYNAMIC)):
+    for name, mode, policy in (("none", pic.LB_NONE, pic.POLICY_KNAPSACK),
+                               ("static", pic.LB_STATIC, pic.POLICY_KNAPSACK),
+                               ("dynamic", pic.LB_DYNAMIC, pic.POLICY_KNAPSACK),
+                               ("dynamic_sfc", pic.LB_DYNAMIC, pic.POLICY_SFC)):
         sim = pic.from_workload(wl, stream=stream.cuda_stream)
-        sim.set_lb_params(mode=mode, interval=interval, theta=0.10, policy=pic.POLICY_KNAPSACK,
+        sim.set_lb_params(mode=mode, interval=interval, theta=0.10, policy=policy,
                           cost=pic.COST_DEVICE_CLOCK, split=args.split, sched=sched)
         sim.set_launch(threads=args.threads or 256, ctas_per_sm=args.ctas_per_sm or 2,
                        precision=args.precision)
@@ -647,6 +652,7 @@ def run_timeline(args):
             "speedup_static_over_none": out["none"]["total_ms"] / out["static"]["total_ms"],
             "speedup_dynamic_over_none": out["none"]["total_ms"] / out["dynamic"]["total_ms"],
             "speedup_dynamic_over_static": out["static"]["total_ms"] / out["dynamic"]["total_ms"],
+            "speedup_knapsack_over_sfc": out["dynamic_sfc"]["total_ms"] / out["dynamic"]["total_ms"],
             "modes": out}
     print(json.dumps(line, default=_jsonable), flush=True)
 

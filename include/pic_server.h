@@ -83,7 +83,8 @@ enum {
     PIC_REQ_ACTIVE = 1,  /* resident, stepping every tick    */
     PIC_REQ_DONE = 2,    /* finished, results resident       */
     PIC_REQ_RELEASED = 3,
-    PIC_REQ_CANCELLED = 4 /* withdrawn by pic_server_cancel */
+    PIC_REQ_CANCELLED = 4, /* withdrawn by pic_server_cancel */
+    PIC_REQ_FAILED = 5     /* could not be admitted (see pic_server_tick) */
 };
 
 pic_status pic_server_create(const pic_server_desc* desc, pic_server** out);
@@ -97,7 +98,11 @@ pic_status pic_server_submit(pic_server* srv, const pic_request_desc* req, int64
  * and the footprint fits, advances every active request by one step (one
  * packed particle launch), and marks requests that reached their step count
  * DONE.  Synchronises the stream.  *n_active and *n_pending (nullable) receive
- * the counts after the tick. */
+ * the counts after the tick.  A request whose admission fails without a
+ * device error (its grid or species rejected by pic_init or pic_add_species,
+ * or their allocation failing) becomes PIC_REQ_FAILED, with the reason in
+ * pic_server_last_error, and the tick goes on with the other requests; a
+ * device error poisons the server (PIC_ECUDA, then PIC_ESTATE). */
 pic_status pic_server_tick(pic_server* srv, int* n_active, int* n_pending);
 
 /* State and host wall-clock times (seconds, steady clock) of a request:

@@ -90,7 +90,7 @@ class ServerStats(ctypes.Structure):
                 ("admitted", _i64), ("finished", _i64), ("bytes_in_use", _i64)]
 
 
-REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED, REQ_CANCELLED = range(5)
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_RELEASED, REQ_CANCELLED, REQ_FAILED = range(6)
 
 # (name, restype, argtypes) of every exported function of include/*.h
 SIGNATURES = [

@@ -392,6 +392,22 @@ double plan_efficiency(const pic_sim* s, const std::vector<double>& costs) {
     return pic::lb_efficiency(uc.data(), P.unit_worker.data(), (int64_t)uc.size(), P.n_workers);
 }
 
+// maps work units to workers with the policy of p (knapsack or Morton SFC)
+void map_units(const pic_sim* s, const pic_lb_params& p, const std::vector<pic::Unit>& units, int nw,
+               std::vector<double>& uc, std::vector<int32_t>& assign) {
+    uc.resize(units.size());
+    for (size_t i = 0; i < units.size(); ++i) uc[i] = units[i].cost;
+    assign.resize(units.size());
+    if (p.policy == PIC_POLICY_KNAPSACK) {
+        pic::knapsack(uc.data(), (int64_t)uc.size(), nw, p.cap_factor, assign.data());
+    } else {
+        std::vector<int32_t> ijk(3 * units.size());
+        for (size_t i = 0; i < units.size(); ++i)
+            for (int a = 0; a < 3; ++a) ijk[3 * i + a] = s->box_ijk[3 * units[i].box + a];
+        pic::sfc(uc.data(), ijk.data(), (int64_t)uc.size(), s->h.dim, nw, assign.data());
+    }
+}
+
 pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_result* out) {
     std::vector<double> costs;
     std::vector<int64_t> np;
@@ -403,17 +419,9 @@ pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_re
     const int split = p.split > 0 ? p.split : s->split;
     std::vector<pic::Unit> units =
         pic::make_units(costs.data(), np.data(), nb, nw, split, 256, true);
-    std::vector<double> uc(units.size());
-    for (size_t i = 0; i < units.size(); ++i) uc[i] = units[i].cost;
-    std::vector<int32_t> assign(units.size());
-    if (p.policy == PIC_POLICY_KNAPSACK) {
-        pic::knapsack(uc.data(), (int64_t)uc.size(), nw, p.cap_factor, assign.data());
-    } else {
-        std::vector<int32_t> ijk(3 * units.size());
-        for (size_t i = 0; i < units.size(); ++i)
-            for (int a = 0; a < 3; ++a) ijk[3 * i + a] = s->box_ijk[3 * units[i].box + a];
-        pic::sfc(uc.data(), ijk.data(), (int64_t)uc.size(), s->h.dim, nw, assign.data());
-    }
+    std::vector<double> uc;
+    std::vector<int32_t> assign;
+    map_units(s, p, units, nw, uc, assign);
     double e_new = pic::lb_efficiency(uc.data(), assign.data(), (int64_t)uc.size(), nw);
     bool adopted = pic::adopt(e_old, e_new, theta);
     if (adopted) {
@@ -517,10 +525,9 @@ pic_status replan(pic_sim* s) {
     const int split = p.split > 0 ? p.split : s->split;
     std::vector<pic::Unit> units = pic::make_units(s->last_costs.data(), s->last_np.data(),
                                                    s->h.nboxes, nw, split, 256, true);
-    std::vector<double> uc(units.size());
-    for (size_t i = 0; i < units.size(); ++i) uc[i] = units[i].cost;
-    std::vector<int32_t> assign(units.size());
-    pic::knapsack(uc.data(), (int64_t)uc.size(), nw, p.cap_factor, assign.data());
+    std::vector<double> uc;
+    std::vector<int32_t> assign;
+    map_units(s, p, units, nw, uc, assign);  // the simulation's own policy
     build_plan(s, units, assign, nw, p.sched);
     return upload_plan(s);
 }
@@ -1178,10 +1185,20 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     const int split_c[3] = {4, 16, 64};
     float best_ms = 1e30f;
     pic_launch_cfg best_cfg{s->threads, s->ctas_per_sm, s->split, 0};
-    cudaEvent_t a, b;
-    CU(s, cudaEventCreate(&a));
-    CU(s, cudaEventCreate(&b));
-    const bool prof = s->profiling;
+    // the events and the profiling switch are restored on every way out
+    struct Guard {
+        pic_sim* s;
+        bool prof;
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Guard() {
+            s->profiling = prof;
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } g{s, s->profiling};
+    CU(s, cudaEventCreate(&g.a));
+    CU(s, cudaEventCreate(&g.b));
+    cudaEvent_t a = g.a, b = g.b;
     s->profiling = false;
     const bool splits = s->lb_set && s->lb.mode != PIC_LB_NONE;
     for (int t : threads_c)
@@ -1203,9 +1220,7 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
                     best_cfg = pic_launch_cfg{t, c, sp, 0};
                 }
             }
-    s->profiling = prof;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    s->profiling = g.prof;
     TRY(pic_set_launch(s, &best_cfg));
     if (best) *best = best_cfg;
     return sync_and_check(s);

@@ -391,7 +391,17 @@ pic_status pic_server_tick(pic_server* s, int* n_active, int* n_pending) {
         if (slot < 0 || s->bytes_in_use + r.footprint > s->desc.hbm_budget_bytes) break;
         s->pending.pop_front();
         pic_status st = admit(s, r, slot);
-        if (st != PIC_OK) return st;
+        if (st != PIC_OK) {
+            // nothing of the request was registered with the server; a device
+            // error poisons it, any other failure fails this request alone
+            if (r.sim) pic_destroy(r.sim);
+            r.sim = nullptr;
+            if (s->poisoned) return st;
+            r.state = PIC_REQ_FAILED;
+            r.t_done = now_s();
+            r.arrays.clear();
+            r.ids.clear();
+        }
     }
     if (s->dirty) {
         pic_status st = rebuild_units(s);

@@ -180,3 +180,20 @@ def test_cancel_pending_and_active_requests():
     with pytest.raises(L.PicError) as ei:
         srv.cancel(10_000)
     assert ei.value.status == L.PIC_EINVAL
+
+
+def test_request_rejected_at_admission_fails_alone():
+    """A request that passes submission but that the simulation set-up rejects
+    (an odd number of cells along x) fails by itself, and the requests behind
+    it are admitted and finish."""
+    srv = Server(dim=2, max_active=2)
+    bad = srv.submit((63, 1, 64), (63, 1, 32), (0.2, 1, 0.2), 5, plasma=dict(ppc=2, seed=1))
+    good = srv.submit((64, 1, 64), (32, 1, 32), (0.2, 1, 0.2), 5, plasma=dict(ppc=2, seed=2))
+    srv.run_until_idle()
+    assert srv.poll(bad)["state"] == L.REQ_FAILED and srv.poll(bad)["t_done"] >= 0
+    assert srv.poll(good)["state"] == L.REQ_DONE
+    assert srv.stats()["bytes_in_use"] == srv.footprint(good)
+    for call in (lambda: srv.cancel(bad), lambda: srv.read_field(bad, L.EX, (63, 1, 64))):
+        with pytest.raises(L.PicError) as ei:
+            call()
+        assert ei.value.status == L.PIC_ESTATE

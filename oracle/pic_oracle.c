@@ -21,7 +21,9 @@
  *     the transpose of the Esirkepov deposit (checked in the pins).
  * Parity with the CUDA path is checked on these definitions; the physics
  * pins (dispersion, gyration, plasma frequency, continuity, Gauss) are in the
- * tests.
+ * tests.  One part is parity unpinned: the damping profile of the absorbing
+ * z layers (damp_factor), a reading with no counterpart in the paper, checked
+ * only for absorbing an outgoing pulse.
  */
 #include "pic_oracle.h"
 #include <math.h>

@@ -42,7 +42,11 @@ enum { ORC_EX = 0, ORC_EY, ORC_EZ, ORC_BX, ORC_BY, ORC_BZ, ORC_JX, ORC_JY, ORC_J
 /* dim: 2 or 3; n: cells (nx, ny, nz) with ny == 1 when dim == 2;
  * d: cell sizes; dt: time step; order: shape order 1, 2 or 3;
  * absorb_cells: 0 = fully periodic; > 0 = width (in z cells) of the damping
- * layers at both z ends, where particles are removed.  Returns NULL on bad input. */
+ * layers at both z ends, where particles are removed.  Returns NULL on bad input.
+ * The layers' damping profile, 1 - (p/absorb)^2 / 2 per step at depth p, is a
+ * reading of this project (the paper fixes no field boundary): parity
+ * unpinned beyond the tests that the layers absorb an outgoing pulse and
+ * remove the particles that enter them. */
 orc_sim* orc_create(int dim, const int64_t n[3], const double d[3], double dt,
                     int order, int absorb_cells);
 void orc_destroy(orc_sim* s);

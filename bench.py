@@ -316,9 +316,10 @@ def run_ours(args, rank, world):
         mixed = dict(arms[2], arithmetic="float-float (FP32 pairs, ~48-bit significand) gather, Boris and "
                                          "deposit weights; FP64 storage, positions and current sums; parity "
                                          "1e-10 vs the FP64 oracle (tests/test_gpu_parity.py)")
-        fp32 = dict(arms[3], arithmetic="FP32 gather, Boris and deposit weights; FP64 storage, positions "
-                                        "and current sums; parity 3e-5 (500 FP32 roundoffs) vs the FP64 "
-                                        "oracle (tests/test_gpu_parity.py)")
+        fp32 = dict(arms[3], arithmetic="FP32 gather, Boris and deposit weights; FP64 storage and positions; "
+                                        "each tile's current summed in FP32, then added to the FP64 grid; "
+                                        "parity 3e-5 (500 FP32 roundoffs) vs the FP64 oracle "
+                                        "(tests/test_gpu_parity.py)")
 
     # ---- the paper's cost strategies side by side (same schedule, same tuning)
     cost_arms = {"device_clock": nparts * args.steps * world / (ms_bal / 1e3)}

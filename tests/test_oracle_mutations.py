@@ -75,6 +75,28 @@ MUTATIONS = [
     ("energy-conserving gather: box shape from floor instead of the nearest node",
      "if (order == 0) return (int64_t)floor(xi + 0.5);", "if (order == 0) return (int64_t)floor(xi);"),
     ("energy-conserving gather: flag ignored", "    s->ec = energy_conserving;\n", "    s->ec = 0;\n"),
+    ("boris: rotation from u- instead of u'", "up[0] = um[0] + (ud[1] * sv[2] - ud[2] * sv[1]);",
+     "up[0] = um[0] + (um[1] * sv[2] - um[2] * sv[1]);"),
+    ("morton 2D: x and z bits swapped",
+     "key |= (uint64_t)((bx >> i) & 1) << (2 * i);\n            key |= (uint64_t)((bz >> i) & 1) << (2 * i + 1);",
+     "key |= (uint64_t)((bx >> i) & 1) << (2 * i + 1);\n            key |= (uint64_t)((bz >> i) & 1) << (2 * i);"),
+    ("esirkepov 2D: out-of-plane current with u_y instead of v_y", "else deposit2d(s, qw, X0, X1, u[1] / g);",
+     "else deposit2d(s, qw, X0, X1, u[1]);"),
+    ("ampere: Jz sign", "F(ORC_EZ, i, j, k) += dt * (cBz - F(ORC_JZ, i, j, k));",
+     "F(ORC_EZ, i, j, k) += dt * (cBz + F(ORC_JZ, i, j, k));"),
+    ("knapsack: box cap ignored", "if (cnt[w] >= cap) continue;", "if (0 && cnt[w] >= cap) continue;"),
+    ("gather: quadratic support from floor(x)", "if (order == 2) return (int64_t)floor(xi + 0.5) - 1;",
+     "if (order == 2) return (int64_t)floor(xi) - 1;"),
+    ("shape: quadratic outer piece without 1/2", "if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);",
+     "if (a < 1.5) return (1.5 - a) * (1.5 - a);"),
+    ("faraday: d(Ey)/dz term dropped from curl_x E",
+     "double cEx = (F(ORC_EZ, i, j + 1, k) - F(ORC_EZ, i, j, k)) * iy -\n"
+     "                             (F(ORC_EY, i, j, k + 1) - F(ORC_EY, i, j, k)) * iz;",
+     "double cEx = (F(ORC_EZ, i, j + 1, k) - F(ORC_EZ, i, j, k)) * iy;"),
+    ("bin: positions outside the domain not wrapped", "c[a] = wrap((int64_t)floor(pos[a] / dd), n[a]) / bsize[a];",
+     "c[a] = ((int64_t)floor(pos[a] / dd) < 0 ? 0 : (int64_t)floor(pos[a] / dd) % n[a]) / bsize[a];"),
+    ("bin: box index with z fastest", "box[p] = (c[2] * nb[1] + c[1]) * nb[0] + c[0];",
+     "box[p] = (c[0] * nb[1] + c[1]) * nb[2] + c[2];"),
 ]
 
 

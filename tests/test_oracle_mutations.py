@@ -97,6 +97,14 @@ MUTATIONS = [
      "c[a] = ((int64_t)floor(pos[a] / dd) < 0 ? 0 : (int64_t)floor(pos[a] / dd) % n[a]) / bsize[a];"),
     ("bin: box index with z fastest", "box[p] = (c[2] * nb[1] + c[1]) * nb[0] + c[0];",
      "box[p] = (c[0] * nb[1] + c[1]) * nb[2] + c[2];"),
+    ("antenna: cosine carrier", "double env = exp(-tt * tt) * sin(s->las_omega * (t - s->las_tpeak));",
+     "double env = exp(-tt * tt) * cos(s->las_omega * (t - s->las_tpeak));"),
+    ("antenna: envelope twice as long", "double tt = (t - s->las_tpeak) / s->las_tau;",
+     "double tt = (t - s->las_tpeak) / (2.0 * s->las_tau);"),
+    ("antenna: waist read as the Gaussian's sigma", "exp(-r2 / (s->las_w0 * s->las_w0));",
+     "exp(-r2 / (2.0 * s->las_w0 * s->las_w0));"),
+    ("antenna: source at t = n dt instead of (n + 1/2) dt", "double t = ((double)s->step + 0.5) * s->dt;",
+     "double t = ((double)s->step) * s->dt;"),
 ]
 
 

@@ -97,6 +97,9 @@ MUTATIONS = [
      "c[a] = ((int64_t)floor(pos[a] / dd) < 0 ? 0 : (int64_t)floor(pos[a] / dd) % n[a]) / bsize[a];"),
     ("bin: box index with z fastest", "box[p] = (c[2] * nb[1] + c[1]) * nb[0] + c[0];",
      "box[p] = (c[0] * nb[1] + c[1]) * nb[2] + c[2];"),
+    ("boris: gamma of u^{n-1/2} instead of u-",
+     "double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);",
+     "double gm = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);"),
     ("antenna: cosine carrier", "double env = exp(-tt * tt) * sin(s->las_omega * (t - s->las_tpeak));",
      "double env = exp(-tt * tt) * cos(s->las_omega * (t - s->las_tpeak));"),
     ("antenna: envelope twice as long", "double tt = (t - s->las_tpeak) / s->las_tau;",

@@ -87,6 +87,27 @@ def test_boris_exact_gyration(q):
     np.testing.assert_allclose(uu, want, atol=2e-12)
 
 
+def test_boris_parallel_fields_rotate_with_the_half_kicked_gamma():
+    """E and B both along z: u_z gains q E dt / m per step exactly (the
+    rotation about z leaves it alone), |u_perp| is conserved, and step n
+    rotates u_perp by -2 atan(k B / gamma-) with k = q dt / (2 m) and gamma-
+    that of u after the first half kick, u_z0 + (2n + 1) k E: the relativistic
+    factor belongs to u-, not to u^{n-1/2} (which would turn the orbit by
+    0.09 rad more here)."""
+    q, m, dt, B, E = -1.0, 1.0, 0.2, 1.3, 0.4
+    k = q * dt / (2 * m)
+    u0 = np.array([0.7, 0.2, 0.5])
+    eb = np.array([0, 0, E, 0, 0, B])
+    u, ang, up2 = u0.copy(), 0.0, u0[0] ** 2 + u0[1] ** 2
+    N = 200
+    for n in range(N):
+        u = orc.boris(q, m, dt, eb, u)
+        ang -= 2 * math.atan(k * B / math.sqrt(1 + up2 + (u0[2] + (2 * n + 1) * k * E) ** 2))
+    want = [u0[0] * math.cos(ang) - u0[1] * math.sin(ang), u0[0] * math.sin(ang) + u0[1] * math.cos(ang),
+            u0[2] + 2 * N * k * E]
+    np.testing.assert_allclose(u, want, rtol=0, atol=1e-11)
+
+
 def test_boris_pure_electric_kick():
     """B = 0: the two half kicks add to q E dt / m exactly."""
     E = np.array([0.3, -0.2, 0.5])

@@ -100,6 +100,12 @@ MUTATIONS = [
     ("boris: gamma of u^{n-1/2} instead of u-",
      "double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);",
      "double gm = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);"),
+    ("field update: E before the first B half step", "    add_antenna(s);\n    push_b_half(s);\n    push_e(s);\n",
+     "    add_antenna(s);\n    push_e(s);\n    push_b_half(s);\n"),
+    ("field update: second B half step dropped", "    push_e(s);\n    push_b_half(s);\n    damp_fields(s);",
+     "    push_e(s);\n    damp_fields(s);"),
+    ("esirkepov: dz for dy in the Jz prefactor", "const double cz = -qw / (dx * dy * dt);",
+     "const double cz = -qw / (dx * dz * dt);"),
     ("antenna: cosine carrier", "double env = exp(-tt * tt) * sin(s->las_omega * (t - s->las_tpeak));",
      "double env = exp(-tt * tt) * cos(s->las_omega * (t - s->las_tpeak));"),
     ("antenna: envelope twice as long", "double tt = (t - s->las_tpeak) / s->las_tau;",

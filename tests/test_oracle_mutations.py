@@ -106,6 +106,11 @@ MUTATIONS = [
      "    push_e(s);\n    damp_fields(s);"),
     ("esirkepov: dz for dy in the Jz prefactor", "const double cz = -qw / (dx * dy * dt);",
      "const double cz = -qw / (dx * dz * dt);"),
+    ("positions: no wrap at the upper end", "    if (x >= L) x -= L;\n    return x;", "    return x;"),
+    ("box counts: positions not wrapped", "c[a] = wrap((int64_t)floor(pos[a] / s->d[a]), s->n[a]) / bsize[a];",
+     "c[a] = ((int64_t)floor(pos[a] / s->d[a]) < 0 ? 0 : (int64_t)floor(pos[a] / s->d[a]) % s->n[a]) / bsize[a];"),
+    ("box counts: x and y box indices swapped", "counts[(c[2] * nb[1] + c[1]) * nb[0] + c[0]]++;",
+     "counts[(c[2] * nb[1] + c[0]) * nb[0] + c[1]]++;"),
     ("antenna: cosine carrier", "double env = exp(-tt * tt) * sin(s->las_omega * (t - s->las_tpeak));",
      "double env = exp(-tt * tt) * cos(s->las_omega * (t - s->las_tpeak));"),
     ("antenna: envelope twice as long", "double tt = (t - s->las_tpeak) / s->las_tau;",

@@ -586,6 +586,36 @@ def test_bin_particles_by_hand():
     assert list(perm) == [0, 3, 5, 2, 4, 6, 1]
 
 
+def test_box_counts_by_hand():
+    """The per-box particle counts of a simulation, for the hand case of the
+    binning test: 4 x 2 x 1 cells of 0.5 in boxes of 2 x 1 x 1; positions just
+    outside the domain count in the periodic image."""
+    sim = orc.OracleSim(3, (4, 2, 1), (0.5, 0.5, 0.5), 0.1, 1)
+    x = [0.2, 1.9, 0.7, 1.2, 0.4, -0.1, 2.0]
+    y = [0.1, 0.9, 0.6, 0.2, 0.8, 0.3, 0.7]
+    sim.add_species(-1.0, 1.0, x, y, [0.1] * 7, [0.0] * 7, [0.0] * 7, [0.0] * 7, [1.0] * 7)
+    assert list(sim.box_counts((2, 1, 1)).ravel()) == [1, 2, 3, 1]
+
+
+def test_periodic_positions_stay_in_the_domain():
+    """Fast particles (|u| up to 3, several cells per step) in a small periodic
+    box: after every step each coordinate lies in [0, L), wrapped at both ends,
+    and none is lost."""
+    rng = np.random.default_rng(7)
+    n, d = (6, 5, 4), (0.3, 0.4, 0.5)
+    L = [n[a] * d[a] for a in range(3)]
+    npart = 400
+    sim = orc.OracleSim(3, n, d, 0.09, 2)
+    sim.add_species(-1.0, 1.0, rng.uniform(0, L[0], npart), rng.uniform(0, L[1], npart),
+                    rng.uniform(0, L[2], npart), *(rng.uniform(-3, 3, (3, npart))), np.full(npart, 1e-3))
+    for _ in range(20):
+        sim.step(1)
+        p = sim.particles(0)
+        assert len(p["x"]) == npart
+        for a, k in enumerate(("x", "y", "z")):
+            assert p[k].min() >= 0.0 and p[k].max() < L[a]
+
+
 # ------------------------------------------- energy-conserving gather ---
 def _gl3_on(f, a, b):
     """3-point Gauss-Legendre on [a, b] (interior nodes only, so a jump at

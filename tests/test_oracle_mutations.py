@@ -111,6 +111,9 @@ MUTATIONS = [
      "c[a] = ((int64_t)floor(pos[a] / s->d[a]) < 0 ? 0 : (int64_t)floor(pos[a] / s->d[a]) % s->n[a]) / bsize[a];"),
     ("box counts: x and y box indices swapped", "counts[(c[2] * nb[1] + c[1]) * nb[0] + c[0]]++;",
      "counts[(c[2] * nb[1] + c[0]) * nb[0] + c[1]]++;"),
+    ("rho: charge density without the cell volume", "double qw = sp->q * sp->w[p] / vol;", "double qw = sp->q * sp->w[p];"),
+    ("rho: shape one order low", "for (int l = 0; l < np1; l++) wt[a][l] = orc_shape(o, X[a] - (double)(b[a] + l));",
+     "for (int l = 0; l < np1; l++) wt[a][l] = orc_shape(o > 1 ? o - 1 : o, X[a] - (double)(b[a] + l));"),
     ("antenna: cosine carrier", "double env = exp(-tt * tt) * sin(s->las_omega * (t - s->las_tpeak));",
      "double env = exp(-tt * tt) * cos(s->las_omega * (t - s->las_tpeak));"),
     ("antenna: envelope twice as long", "double tt = (t - s->las_tpeak) / s->las_tau;",

@@ -703,7 +703,7 @@ def main():
         c3 = run_c3(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=6)
+        r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=15)
         cpu = {"value": r, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                "sample": sample + " (%.1f s of CPU time)" % secs}
     if rank == 0:

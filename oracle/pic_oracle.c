@@ -21,9 +21,10 @@
  *     the transpose of the Esirkepov deposit (checked in the pins).
  * Parity with the CUDA path is checked on these definitions; the physics
  * pins (dispersion, gyration, plasma frequency, continuity, Gauss) are in the
- * tests.  One part is parity unpinned: the damping profile of the absorbing
- * z layers (damp_factor), a reading with no counterpart in the paper, checked
- * only for absorbing an outgoing pulse.
+ * tests.  The damping profile of the absorbing z layers (damp_factor) is a
+ * reading with no counterpart in the paper (it fixes no field boundary); the
+ * tests pin it layer by layer, bit for bit, against hand-computed factors on a
+ * uniform field, besides checking that the layers absorb an outgoing pulse.
  */
 #include "pic_oracle.h"
 #include <math.h>

@@ -116,6 +116,32 @@ def test_absorbing_boundary_and_laser_parity(dim, order):
     assert sim.num_particles(0) < 3000
 
 
+@pytest.mark.parametrize("dim", [3, 2])
+def test_damping_profile_exact_on_a_uniform_field(dim):
+    """The damping kernel against the hand-computed layer factors of the
+    absorbing-layer reading (tests/golden/damping_profile.json), bit for bit:
+    a uniform field is curl-free, so one step changes it only in the layers."""
+    import json
+    import os
+    from fractions import Fraction
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "damping_profile.json")))
+    A, nz, fac = g["A"], g["nz"], [Fraction(x) for x in g["factor_by_layer"]]
+    n = (8, 8 if dim == 3 else 1, nz)
+    box = (8, 8 if dim == 3 else 1, 8)
+    sim = pic.Simulation(dim, n, box, (0.5, 0.5 if dim == 3 else 1.0, 0.5), dt=0.2, absorb_cells=A)
+    values = [1.0, -2.0, 0.5, 0.25, -1.5, 3.0]
+    for c, v in enumerate(values):
+        sim.set_field(c, np.full((n[2], n[1], n[0]), v))
+    sim.step(1)
+    sim.sync()
+    for c, v in enumerate(values):
+        f = sim.read_field(c)
+        for k in range(nz):
+            want = float(Fraction(v) * fac[k])
+            assert np.all(f[k] == want), (c, k, np.unique(f[k]), want)
+    sim.close()
+
+
 def test_lognormal_uneven_boxes_parity_with_balancing():
     wl = workloads.lognormal(seed=5, nbox=(4, 4, 4), box=8, median=1500.0, sigma=1.0, order=2)
     sim, ref = make_gpu(wl), make_oracle(wl)

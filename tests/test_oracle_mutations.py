@@ -65,6 +65,11 @@ MUTATIONS = [
     ("threshold: strict improvement", "return e_new >= (1.0 + theta) * e_old;", "return e_new > (1.0 + theta) * e_old;"),
     ("antenna: sheet amplitude without factor 2", "double amp = 2.0 * s->las_a0 / s->d[2] * env;",
      "double amp = s->las_a0 / s->d[2] * env;"),
+    ("damping: profile linear in the depth", "    return 1.0 - 0.5 * r * r;\n}", "    return 1.0 - 0.5 * r;\n}"),
+    ("damping: factor 1/2 dropped", "    return 1.0 - 0.5 * r * r;\n}", "    return 1.0 - r * r;\n}"),
+    ("damping: depth counted from 0",
+     "if (k < A) p = A - k;\n    else if (k > s->n[2] - 1 - A) p = k - (s->n[2] - 1 - A);",
+     "if (k < A) p = A - 1 - k;\n    else if (k > s->n[2] - 1 - A) p = k - (s->n[2] - A);"),
     ("damping layer disabled", "if (s->absorb <= 0) return;\n    for (int64_t k = 0;", "return;\n    for (int64_t k = 0;"),
     ("particles: upper absorbing boundary ignored", "if (np_[2] < zlo || np_[2] >= zhi) drop[ndrop++] = p;",
      "if (np_[2] < zlo) drop[ndrop++] = p;"),

@@ -10,6 +10,7 @@ import itertools
 import json
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -383,6 +384,35 @@ def test_damping_layer_absorbs_outgoing_pulse():
     sim.step(260)
     e_end = sum(float((sim.field(c) ** 2).sum()) for c in range(6))
     assert e_mid > 0 and e_end < 0.05 * e_mid
+
+
+@pytest.mark.parametrize("dim,which", [(3, "A4"), (2, "A4"), (3, "A8")])
+def test_damping_profile_exact_on_a_uniform_field(dim, which):
+    """The damping profile layer by layer, bit for bit.  A uniform field is
+    curl-free, so with no particles and no laser one step leaves E and B
+    unchanged exactly until the layers scale them: afterwards every component
+    in cell layer k must equal its uniform value times the hand-computed factor
+    of the absorbing-layer reading (tests/golden/damping_profile.json: 1/2 in
+    the outermost layer of each end, 1 inside the domain).  The values are
+    exact binary fractions, so a profile linear in the depth, a dropped 1/2,
+    a depth counted from 0 or a layer at the wrong end all fail."""
+    g = json.load(open(os.path.join(HERE, "golden", "damping_profile.json")))
+    if which == "A4":
+        A, nz, fac = g["A"], g["nz"], [Fraction(x) for x in g["factor_by_layer"]]
+    else:
+        A, nz, fac = 8, g["A8_nz"], [Fraction(x) for x in g["A8_factor_by_layer"]]
+    n = (4, 4 if dim == 3 else 1, nz)
+    d = (0.5, 0.5 if dim == 3 else 1.0, 0.5)
+    sim = orc.OracleSim(dim, n, d, 0.2, 1, absorb_cells=A)
+    values = [1.0, -2.0, 0.5, 0.25, -1.5, 3.0]  # Ex Ey Ez Bx By Bz
+    for c, v in enumerate(values):
+        sim.set_field(c, np.full((n[2], n[1], n[0]), v))
+    sim.step(1)
+    for c, v in enumerate(values):
+        f = sim.field(c)
+        for k in range(nz):
+            want = float(Fraction(v) * fac[k])
+            assert np.all(f[k] == want), (c, k, np.unique(f[k]), want)
 
 
 def test_absorbed_particles_are_removed_by_id():

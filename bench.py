@@ -1,13 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 PIC step with in-situ cost measurement and dynamic
-load balancing (the method of arXiv 2104.11385) on the 3D laser-foil workload:
-256^3 cells in 512 boxes of 32^3, a hydrogen foil 8 cells thick at 30 n_c with
-64 electrons + 64 protons per foil cell (67.1M particles), a0 = 20 laser, FP64.
+load balancing (the method of arXiv 2104.11385).
 
-One step = one full PIC cycle (per-tile sort, TMA tile staging, gather, Boris
-push, Esirkepov deposit with clock64 box costs, Yee update, boundaries) plus
-the load-balancing routine every 10 steps (dynamic, knapsack, device-clock
-costs, threshold 10 %).  Prints one JSON line.
+Headline workload: the 3D laser-foil at scale, 512 x 512 x 1024 cells in 8192
+boxes of 32^3, a hydrogen foil 16 cells thick at 30 n_c with 64 electrons + 64
+protons per foil cell (536,870,912 particles), a0 = 20 laser, FP64, load
+balancing every 20 steps.  One step = one full PIC cycle (per-tile sort, TMA
+tile staging, gather, Boris push, Esirkepov deposit with clock64 box costs, Yee
+update, boundaries) plus the load-balancing routine at its interval (dynamic,
+knapsack, device-clock costs, threshold 10 %).  Beside it: the 256^3 foil, the
+4096 log-normal boxes, the serving recipe (1000 2D3V requests) and the FP64 CPU
+oracle on the host cores.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -33,8 +36,10 @@ sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
-# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak from unit counts and clocks, for context beside the measured one:
+# SMs x 2 DFMA lanes/clk/SM x 2 flop x 2.07 GHz (the SM count read from the device)
+FP64_LANES_PER_SM_CLK = 2
+SM_MAX_GHZ = 2.07
 # algorithmic FP64 flops per particle update, in-cell path (3D linear: gather 126,
 # local positions and half-node shifts 6, Boris push 70, Esirkepov deposit 73, positions 3)
 FLOPS_PER_PARTICLE = {(3, 1): 275.0, (3, 2): 763.0, (3, 3): 1591.0, (2, 1): 168.0, (2, 2): 348.0,
@@ -98,8 +103,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="foil256",
+    ap.add_argument("--workload", default="foil_at_scale",
                     choices=["foil256", "uniform32", "lognormal4096", "laser_ion_2d", "foil_at_scale"])
+    ap.add_argument("--secondary", default="foil256", choices=["foil256", "none"],
+                    help="a second, compact line of arms on the 256^3 foil")
     ap.add_argument("--scale", type=int, default=1, help="divide the workload extents (small cases for profiling)")
     ap.add_argument("--sched", default="queue", choices=["lists", "queue"])
     ap.add_argument("--split", type=int, default=0, help="work units per worker (0: library default)")
@@ -112,9 +119,13 @@ def parse():
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--no-cost-arms", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
-    ap.add_argument("--server-requests", type=int, default=48)
-    ap.add_argument("--server-steps-max", type=int, default=400,
-                    help="request lengths U[100, max] steps (the serving recipe's full range is 2000)")
+    ap.add_argument("--static-steps", type=int, default=5,
+                    help="timed steps of the no-balancing arm (about 8x slower per step than the balanced one)")
+    ap.add_argument("--server-requests", type=int, default=1000)
+    ap.add_argument("--server-steps-max", type=int, default=2000,
+                    help="request lengths U[100, max] steps (the serving recipe's range is 100..2000)")
+    ap.add_argument("--server-half", action="store_true",
+                    help="also serve the mix with Poisson arrivals at 0.5x the saturated rate")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--timeline", type=int, default=0,
                     help="instead of the bench line: N steps of the workload under each load-balancing mode "
@@ -151,9 +162,13 @@ def make_workload(name, scale, seed_offset=0):
     if name == "laser_ion_2d":
         return W.laser_ion_2d(seed=6 + seed_offset, scale=scale)
     if name == "foil_at_scale":
-        return W.foil_at_scale(seed=5 + seed_offset)
+        return W.foil_at_scale(seed=5 + seed_offset, scale=scale)
     n = max(2, 16 // scale)  # scale > 1: fewer boxes of the same recipe
     return W.lognormal(seed=3 + seed_offset, nbox=(n, n, n))
+
+
+def lb_interval(wl):
+    return int(wl.get("lb_interval", 10))
 
 
 def workload_desc(wl):
@@ -162,9 +177,20 @@ def workload_desc(wl):
         "workload": wl["name"], "cells": list(wl["ncell"]), "box": list(wl["box"]),
         "boxes": int(math.prod(wl["ncell"][a] // wl["box"][a] for a in range(3))),
         "particles": nparts, "species": len(wl["species"]), "shape_order": wl["order"],
-        "lb": "dynamic knapsack, device-clock costs, interval 10, theta 0.10",
+        "lb": "dynamic knapsack, device-clock costs, interval %d, theta 0.10" % lb_interval(wl),
         "l2": "inputs larger than L2 (particle state %.1f GB)" % (nparts * 64 / 1e9),
     }
+
+
+def fp64_peak():
+    """The FP64 FMA throughput of this GPU, measured by libpic's probe (a DFMA
+    loop timed with CUDA events), and the unit-count figure beside it."""
+    import torch
+    from paper_2104_11385_gb300.sim import probe_fp64_fma
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    measured = probe_fp64_fma(20000)
+    nominal = nsm * FP64_LANES_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9 / 1e12
+    return measured, nominal, nsm
 
 
 class ClockSampler:
@@ -218,21 +244,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def run_ours(args, rank, world):
+def run_ours(args, rank, world, wl=None, full=True):
+    """All arms of one workload.  full=False runs the compact set (balanced,
+    float-float, FP32, static order) used for the secondary workload."""
     import numpy as np
     import torch
     import paper_2104_11385_gb300 as pic
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    wl = make_workload(args.workload, args.scale, seed_offset=rank)
-    args.sched_name = args.sched
+    if wl is None:
+        wl = make_workload(args.workload, args.scale, seed_offset=rank)
     nparts = sum(len(s["x"]) for s in wl["species"])
     ncells = int(math.prod(wl["ncell"]))
     stream = torch.cuda.Stream()
-    lbkw = dict(mode=pic.LB_DYNAMIC, interval=10, theta=0.10, policy=pic.POLICY_KNAPSACK,
-                cost=pic.COST_DEVICE_CLOCK, split=args.split,
-                sched=pic.SCHED_QUEUE if args.sched == "queue" else pic.SCHED_LISTS)
+    interval = lb_interval(wl)
+    sched = pic.SCHED_QUEUE if args.sched == "queue" else pic.SCHED_LISTS
+    lbkw = dict(mode=pic.LB_DYNAMIC, interval=interval, theta=0.10, policy=pic.POLICY_KNAPSACK,
+                cost=pic.COST_DEVICE_CLOCK, split=args.split, sched=sched)
 
     def barrier():
         if world > 1:
@@ -248,6 +277,23 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         barrier()
         return max_over_ranks(e0.elapsed_time(e1), world)
+
+    def rate(ms, k):
+        return nparts * k * world / (ms / 1e3)
+
+    def release(sim):
+        sim.close()
+        torch.cuda.empty_cache()
+
+    def profiled(sim, k):
+        sim.set_profiling(True)
+        sim.step(k)
+        st = sim.stats()
+        sim.set_profiling(False)
+        return st
+
+    def per_step(st, key):
+        return st[key] / max(st["steps"], 1)
 
     # ---- balanced (the paper's dynamic load balancing, on the SMs)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
@@ -266,63 +312,109 @@ def run_ours(args, rank, world):
         ms_bal = timed(sim, args.steps)
     clocks = cs.summary()
     lb_timed = sim.lb_log()[nlog0:]  # the load-balancing calls made inside the timed steps
-    # kernel-level timing (CUDA events on the library's stream around each launch)
-    sim.set_profiling(True)
-    sim.step(min(args.steps, 10))
-    st = sim.stats()
-    sim.set_profiling(False)
+    # kernel-level timing: the same number of steps again, with CUDA events on
+    # the library's stream around each launch
+    st = profiled(sim, args.steps)
     kernels_per_step = st["launches"] / max(st["steps"], 1)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
+    release(sim)
+    tkw = {k: tuned[k] for k in ("threads", "ctas_per_sm", "split")}
 
-    # ---- the other schedule kind, for the side-by-side line
-    other = "lists" if args.sched == "queue" else "queue"
-    sim = pic.from_workload(wl, stream=stream.cuda_stream)
-    okw = dict(lbkw, sched=pic.SCHED_LISTS if other == "lists" else pic.SCHED_QUEUE)
-    sim.step(1)
-    sim.rebalance(**dict(okw, theta=0.0))
-    sim.set_lb_params(**okw)
-    sim.step(args.warmup)
-    ms_other = timed(sim, args.steps)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
-
-    # ---- the mixed-precision variant (float-float push, FP64 storage and sums)
-    mixed, fp32 = None, None
+    # ---- reduced-precision variants (float-float push; FP32 push with FP32 tile sums)
+    variants = {}
     if not args.no_mixed and args.precision == 1:
-        arms = {}
         for prec in (2, 3):
             sim = pic.from_workload(wl, stream=stream.cuda_stream)
             sim.set_launch(precision=prec)
             sim.step(1)
             sim.rebalance(**dict(lbkw, theta=0.0))
             sim.set_lb_params(**lbkw)
-            mtuned = sim.autotune(steps_per_candidate=2)
+            vtuned = sim.autotune(steps_per_candidate=2)
             sim.step(args.warmup)
             ms_v = timed(sim, args.steps)
-            sim.set_profiling(True)
-            sim.step(min(args.steps, 10))
-            mst = sim.stats()
-            sim.close()
-            del sim
-            torch.cuda.empty_cache()
-            v = nparts * args.steps * world / (ms_v / 1e3)
-            arms[prec] = {"value": v, "unit": "particle-updates/s", "ms_per_step": ms_v / args.steps,
-                          "particle_kernel_ms": mst["ms_particle"] / max(mst["steps"], 1), "launch": mtuned,
-                          "hbm_frac": BYTES_PER_PARTICLE * nparts / (mst["ms_particle"] / max(mst["steps"], 1)
-                                                                    / 1e3) / 1e9 / hbm_peak_gbs()}
-        mixed = dict(arms[2], arithmetic="float-float (FP32 pairs, ~48-bit significand) gather, Boris and "
-                                         "deposit weights; FP64 storage, positions and current sums; parity "
-                                         "1e-10 vs the FP64 oracle (tests/test_gpu_parity.py)")
-        fp32 = dict(arms[3], arithmetic="FP32 gather, Boris and deposit weights; FP64 storage and positions; "
-                                        "each tile's current summed in FP32, then added to the FP64 grid; "
-                                        "parity 3e-5 (500 FP32 roundoffs) vs the FP64 oracle "
-                                        "(tests/test_gpu_parity.py)")
+            vst = profiled(sim, args.steps)
+            release(sim)
+            kms = per_step(vst, "ms_particle")
+            variants[prec] = {"value": rate(ms_v, args.steps), "unit": "particle-updates/s",
+                              "ms_per_step": ms_v / args.steps, "particle_kernel_ms": kms, "launch": vtuned,
+                              "phase_ms_per_step": {"particle": kms, "fields": per_step(vst, "ms_fields"),
+                                                    "sort": per_step(vst, "ms_sort")},
+                              "hbm_frac": BYTES_PER_PARTICLE * nparts / (kms / 1e3) / 1e9 / hbm_peak_gbs()}
+        variants[2]["arithmetic"] = ("float-float (FP32 pairs, ~48-bit significand) gather, Boris and deposit "
+                                     "weights; FP64 storage, positions and current sums; parity 1e-10 vs the "
+                                     "FP64 oracle (tests/test_gpu_parity.py)")
+        variants[3]["arithmetic"] = ("FP32 gather, Boris and deposit weights; FP64 storage and positions; each "
+                                     "tile's current summed in FP32, then added to the FP64 grid; parity 3e-5 "
+                                     "(500 FP32 roundoffs) vs the FP64 oracle (tests/test_gpu_parity.py)")
+
+    # ---- static box order (no load balancing: the fixed starting mapping)
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    sim.set_launch(threads=tuned["threads"], ctas_per_sm=tuned["ctas_per_sm"], precision=args.precision)
+    sim.step(1 + min(args.warmup, 2))
+    ks = max(1, args.static_steps)
+    ms_static = timed(sim, ks)
+    release(sim)
+    static = {"value": rate(ms_static, ks), "ms_per_step": ms_static / ks, "timed_steps": ks,
+              "speedup_balanced_over_static": (ms_static / ks) / (ms_bal / args.steps),
+              "what": "mode NONE: one unit per box, fixed equal-count Morton mapping, per-worker lists"}
+
+    out = {"value": rate(ms_bal, args.steps), "ms_per_step": ms_bal / args.steps, "clocks": clocks,
+           "gpu_launches": int(round(kernels_per_step * args.steps)), "static_order": static,
+           "mixed_precision": variants.get(2), "fp32": variants.get(3),
+           "config": dict(workload_desc(wl), sched=args.sched, launch=tuned), "launch": tuned}
+    ms_part = per_step(st, "ms_particle")
+    out["phase_ms_per_step"] = {"particle": ms_part, "fields": per_step(st, "ms_fields"),
+                                "sort": per_step(st, "ms_sort")}
+    out["cell_updates_per_s"] = ncells * args.steps * world / (ms_bal / 1e3)
+    out["fdtd_cell_updates_per_s"] = ncells / (per_step(st, "ms_fields") / 1e3)
+    out["lb"] = {"calls_in_timed_steps": len(lb_timed), "adopted": sum(1 for r in lb_timed if r["adopted"]),
+                 "last": lb_timed[-1] if lb_timed else None}
+    out["_nparts"] = nparts
+    if not full:
+        return out
+
+    # ---- the other schedule kind, for the side-by-side line
+    other = "lists" if args.sched == "queue" else "queue"
+    sim = pic.from_workload(wl, stream=stream.cuda_stream)
+    okw = dict(lbkw, sched=pic.SCHED_LISTS if other == "lists" else pic.SCHED_QUEUE)
+    sim.set_launch(**tkw, precision=args.precision)
+    sim.step(1)
+    sim.rebalance(**dict(okw, theta=0.0))
+    sim.set_lb_params(**okw)
+    sim.step(args.warmup)
+    ms_other = timed(sim, args.steps)
+    release(sim)
+    out["other_schedule"] = {"sched": other, "value": rate(ms_other, args.steps),
+                             "ms_per_step": ms_other / args.steps}
+
+    # ---- cutting against ordering: the balanced arm's work units (heavy boxes
+    # cut by the measured costs, the autotuned split) mapped once and never
+    # again, pulled from the queue either in box-index order (no cost input in
+    # the order) or longest-first (the knapsack's cost order)
+    order_arms = {}
+    for name, policy in (("static_units_box_order", pic.POLICY_BOX_ORDER),
+                         ("static_units_lpt_order", pic.POLICY_KNAPSACK)):
+        sim = pic.from_workload(wl, stream=stream.cuda_stream)
+        sim.set_launch(**tkw, precision=args.precision)
+        sim.step(1)
+        r = sim.rebalance(**dict(lbkw, policy=policy, theta=0.0, sched=pic.SCHED_QUEUE,
+                                 split=tuned["split"]))
+        sim.step(args.warmup)
+        ms_o = timed(sim, args.steps)
+        release(sim)
+        order_arms[name] = {"value": rate(ms_o, args.steps), "ms_per_step": ms_o / args.steps,
+                            "units": r["n_units"], "adopted": r["adopted"]}
+    nb = order_arms["static_units_box_order"]["ms_per_step"]
+    nl = order_arms["static_units_lpt_order"]["ms_per_step"]
+    order_arms["speedup_cutting"] = static["ms_per_step"] / nb
+    order_arms["speedup_lpt_order_over_box_order"] = nb / nl
+    order_arms["speedup_dynamic_over_static_lpt"] = nl / out["ms_per_step"]
+    order_arms["what"] = ("static_order -> static_units_box_order: cutting heavy boxes alone; -> "
+                          "static_units_lpt_order: the same units in cost order; -> balanced: remapping every "
+                          "interval with fresh device-clock costs")
+    out["cutting_vs_ordering"] = order_arms
 
     # ---- the paper's cost strategies side by side (same schedule, same tuning)
-    cost_arms = {"device_clock": nparts * args.steps * world / (ms_bal / 1e3)}
+    cost_arms = {"device_clock": out["value"]}
     if not args.no_cost_arms:
         # the heuristic needs no device capture: with capture off the same
         # mappings run without the clock64 / %globaltimer work, which is the
@@ -336,24 +428,14 @@ def run_ours(args, rank, world):
             sim.step(1)
             sim.rebalance(**dict(ckw, theta=0.0))
             sim.set_lb_params(**ckw)
-            sim.set_launch(**{k: tuned[k] for k in ("threads", "ctas_per_sm", "split")}, precision=args.precision)
+            sim.set_launch(**tkw, precision=args.precision)
             sim.step(args.warmup)
-            cost_arms[name] = nparts * args.steps * world / (timed(sim, args.steps) / 1e3)
-            sim.close()
-            del sim
-            torch.cuda.empty_cache()
+            cost_arms[name] = rate(timed(sim, args.steps), args.steps)
+            release(sim)
         cost_arms["capture_overhead"] = cost_arms["heuristic_no_capture"] / cost_arms["heuristic"] - 1.0
-
-    # ---- static box order (no load balancing: the fixed starting mapping)
-    sim = pic.from_workload(wl, stream=stream.cuda_stream)
-    sim.step(1 + args.warmup)
-    ms_static = timed(sim, args.steps)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
+    out["cost_strategies"] = cost_arms
 
     # ---- end to end through the public API with host buffers
-    e2e = None
     if not args.no_e2e:
         pinned = []
         for s in wl["species"]:
@@ -370,6 +452,7 @@ def run_ours(args, rank, world):
             sim.add_species(s["q"], s["m"], p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"], p["w"], ids=p["id"])
         L = wl["laser"]
         sim.add_laser(L["a0"], L["w0"], L["tau"], L["t_peak"], L["omega"], L["xc"], L["yc"], L["k_ant"])
+        sim.set_launch(**tkw, precision=args.precision)
         sim.step(1)
         sim.rebalance(**dict(lbkw, theta=0.0))
         sim.set_lb_params(**lbkw)
@@ -384,63 +467,45 @@ def run_ours(args, rank, world):
         t1 = time.perf_counter()
         d2h += out_e.numel() * 8
         sim.close()
+        del pinned
         secs = max_over_ranks(t1 - t0, world)
-        e2e = {"value": nparts * (args.steps + 1) * world / secs, "unit": "particle-updates/s",
-               "h2d_bytes_per_step": int(h2d / (args.steps + 1)),
-               "d2h_bytes_per_step": int(d2h / (args.steps + 1)),
-               "what": "pic_init + pic_add_species from pinned host arrays (the run's input, amortised over "
-                       "its steps) + 1 step + rebalance + K steps, each followed by reading its per-box costs "
-                       "and counts back, + Ex back at the end"}
+        out["e2e"] = {"value": nparts * (args.steps + 1) * world / secs, "unit": "particle-updates/s",
+                      "h2d_bytes_per_step": int(h2d / (args.steps + 1)),
+                      "d2h_bytes_per_step": int(d2h / (args.steps + 1)),
+                      "what": "pic_init + pic_add_species from pinned host arrays (the run's input, amortised over "
+                              "its steps) + 1 step + rebalance + K steps, each followed by reading its per-box "
+                              "costs and counts back, + Ex back at the end"}
 
-    value = nparts * args.steps * world / (ms_bal / 1e3)
-    static_value = nparts * args.steps * world / (ms_static / 1e3)
-    ms_part = st["ms_particle"] / max(st["steps"], 1)
+    # ---- roofline of the dominant kernel (the particle kernel)
     flops = FLOPS_PER_PARTICLE[(wl["dim"], wl["order"])] * nparts
     achieved_tf = flops / (ms_part / 1e3) / 1e12
-    hbm = HBM_FALLBACK_GBS
-    peak_src = "fallback"
-    try:
-        hbm = float(json.load(open(MEASURED))["hbm_gbs"])
-        peak_src = "measured"
-    except Exception:
-        pass
+    hbm = hbm_peak_gbs()
+    peak_src = "measured" if os.path.exists(MEASURED) else "fallback"
     hbm_achieved = BYTES_PER_PARTICLE * nparts / (ms_part / 1e3) / 1e9
     hbm_obj = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE}
     kname = "pic_particle_kernel<%d,%d> (gather+Boris+Esirkepov+cost)" % (wl["dim"], wl["order"])
     if args.precision == 1:
-        # the FP64 kernel is bound by the FP64 pipe: algorithmic flops against its peak
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": _traffic_per_launch(wl, nparts),
-                    "kernel": kname,
-                    "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.19 TFLOP/s)",
-                    "hbm": hbm_obj}
+        # the FP64 kernel is bound by the FP64 pipe: algorithmic flops against
+        # the FP64 FMA throughput measured here
+        measured, nominal, nsm = fp64_peak()
+        out["roofline"] = {"bound": "alu", "achieved": achieved_tf, "peak": measured, "unit": "TFLOP/s",
+                           "frac": achieved_tf / measured, "traffic": _traffic_per_launch(wl, nparts),
+                           "kernel": kname,
+                           "peak_note": ("FP64 pipe, measured: pic_probe_fp64_fma (DFMA chains on every SM, "
+                                         "CUDA events) %.3f TFLOP/s; from unit counts %d SMs x %d DFMA lanes/clk "
+                                         "x 2 flop x %.2f GHz = %.3f TFLOP/s"
+                                         % (measured, nsm, FP64_LANES_PER_SM_CLK, SM_MAX_GHZ, nominal)),
+                           "frac_of_unit_count_peak": achieved_tf / nominal,
+                           "algorithmic_flop_per_particle": FLOPS_PER_PARTICLE[(wl["dim"], wl["order"])],
+                           "hbm": hbm_obj}
     else:
         # float-float and FP32 leave the FP64 pipe nearly idle: report the particle
         # bytes against HBM (the traffic capture is of the FP64 kernel, so none here)
-        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": hbm_achieved / hbm, "traffic": None, "kernel": kname,
-                    "peak_note": "%s HBM copy bandwidth" % peak_src}
-    return {
-        "value": value, "ms_per_step": ms_bal / args.steps, "clocks": clocks, "e2e": e2e,
-        "gpu_launches": int(round(kernels_per_step * args.steps)),
-        "roofline": roofline,
-        "static_order": {"value": static_value, "ms_per_step": ms_static / args.steps,
-                         "speedup_balanced_over_static": ms_static / ms_bal,
-                         "what": "mode NONE: one unit per box, fixed equal-count Morton mapping, per-worker lists"},
-        "other_schedule": {"sched": other, "value": nparts * args.steps * world / (ms_other / 1e3),
-                           "ms_per_step": ms_other / args.steps},
-        "cost_strategies": cost_arms,
-        "mixed_precision": mixed, "fp32": fp32,
-        "cell_updates_per_s": ncells * args.steps * world / (ms_bal / 1e3),
-        "phase_ms_per_step": {"particle": ms_part, "fields": st["ms_fields"] / max(st["steps"], 1),
-                              "sort": st["ms_sort"] / max(st["steps"], 1)},
-        "fdtd_cell_updates_per_s": ncells / (st["ms_fields"] / max(st["steps"], 1) / 1e3),
-        "lb": {"calls_in_timed_steps": len(lb_timed),
-               "adopted": sum(1 for r in lb_timed if r["adopted"]),
-               "last": lb_timed[-1] if lb_timed else None},
-        "config": dict(workload_desc(wl), sched=args.sched, launch=tuned),
-    }
+        out["roofline"] = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                           "frac": hbm_achieved / hbm, "traffic": None, "kernel": kname,
+                           "peak_note": "%s HBM copy bandwidth" % peak_src}
+    return out
 
 
 def run_c3(args, steps=10):
@@ -502,11 +567,11 @@ def run_c3(args, steps=10):
 
 
 def run_server(args, seed=4):
-    """Serving arm: independent 2D3V thermal-plasma requests (grid side in
-    {64,128,256,512}, ppc in {1,..,64}, steps U[100, max]; max = 400 by default,
-    the serving workload with shortened runs, 2000 for the full recipe) through the continuous-batching server; first all at
-    once (saturated throughput), then Poisson arrivals at 0.8x and 0.5x that
-    rate."""
+    """Serving arm: independent 2D3V thermal-plasma requests (the serving
+    recipe: 1000 requests, grid side in {64,128,256,512}, ppc in {1,..,64},
+    steps U[100, 2000]) through the continuous-batching server; first all at
+    once (saturated throughput), then Poisson arrivals at 0.8x that rate (and
+    at 0.5x with --server-half)."""
     import numpy as np
     from paper_2104_11385_gb300.server import Server
     from paper_2104_11385_gb300 import _lib as L
@@ -548,9 +613,12 @@ def run_server(args, seed=4):
     wall_sat, lat_sat, st_sat = serve([0.0] * n)
     sat_rate = n / wall_sat
     out = {"requests": n,
-           "mix": "2D3V, side {64..512}, ppc {1..64}, steps U[100,%d], 32x32 boxes" % args.server_steps_max,
+           "mix": "2D3V, side {64..512}, ppc {1..64}, steps U[100,%d], 32x32 boxes, FP64, linear" % args.server_steps_max,
+           "particle_updates": int(work),
            "saturated_requests_per_s": sat_rate, "saturated_particle_updates_per_s": work / wall_sat}
-    for frac in (0.8, 0.5):
+    out["arrival_rates"] = "0.8x and 0.5x the saturated rate" if args.server_half else (
+        "0.8x the saturated rate (the 0.5x pass is left out of the default run for time: --server-half)")
+    for frac in ((0.8, 0.5) if args.server_half else (0.8,)):
         lam = frac * sat_rate
         arr = np.cumsum(rng.exponential(1.0 / lam, n))
         arr -= arr[0]
@@ -566,21 +634,27 @@ def run_server(args, seed=4):
     return out
 
 
-def oracle_rate(wl_name, budget_s=15.0, steps=1):
-    """The FP64 CPU oracle as it stands, on a bounded sample of the workload:
-    the same recipe at 1/4 of the extents (1/64 of the cells, the foil 2 cells
-    thick), timed over `steps` full PIC cycles on one host core."""
-    import oracle as orc
+def _oracle_sample(wl_name, seed_offset=0):
+    """A bounded sample of the workload for the CPU oracle: the same recipe at
+    reduced extents (the full ones take minutes per step on one core)."""
     from paper_2104_11385_gb300 import workloads as W
-    if wl_name in ("foil256", "foil_at_scale"):
-        wl = W.foil256(seed=2, scale=4)
-        sample = "foil256 recipe at 1/4 extents: 64^3 cells, foil 2 cells thick, %d particles, %d step(s)"
-    elif wl_name == "uniform32":
-        wl = W.uniform32(seed=1)
-        sample = "uniform32 in full: 32^3 cells, %d particles, %d step(s)"
-    else:
-        wl = W.lognormal(seed=3, nbox=(4, 4, 4))
-        sample = "lognormal recipe on 4^3 boxes of 16^3: %d particles, %d step(s)"
+    if wl_name == "foil_at_scale":
+        return (W.foil_at_scale(seed=5 + seed_offset, scale=8),
+                "foil-at-scale recipe at 1/8 extents: 64x64x128 cells, foil 2 cells thick, 64 ppc per species")
+    if wl_name == "foil256":
+        return W.foil256(seed=2 + seed_offset, scale=4), "foil256 recipe at 1/4 extents: 64^3 cells, foil 2 cells thick"
+    if wl_name == "uniform32":
+        return W.uniform32(seed=1 + seed_offset), "uniform32 in full: 32^3 cells"
+    if wl_name == "laser_ion_2d":
+        return W.laser_ion_2d(seed=6 + seed_offset, scale=8), "laser-ion 2D recipe at 1/8 extents: 240^2 cells"
+    return W.lognormal(seed=3 + seed_offset, nbox=(4, 4, 4)), "lognormal recipe on 4^3 boxes of 16^3"
+
+
+def oracle_rate(wl_name, budget_s=15.0, steps=1, seed_offset=0):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the workload,
+    timed over up to `steps` full PIC cycles within budget_s on one host core."""
+    import oracle as orc
+    wl, sample = _oracle_sample(wl_name, seed_offset)
     ref = orc.OracleSim(wl["dim"], wl["ncell"], wl["dx"], wl["dt"], wl["order"], wl["absorb"])
     for s in wl["species"]:
         ref.add_species(s["q"], s["m"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["id"])
@@ -596,7 +670,55 @@ def oracle_rate(wl_name, budget_s=15.0, steps=1):
         if time.perf_counter() - t0 > budget_s:
             break
     secs = time.perf_counter() - t0
-    return nparts * done / secs, sample % (nparts, done), secs
+    return nparts * done / secs, "%s, %d particles, %d step(s)" % (sample, nparts, done), secs
+
+
+def _oracle_worker(task):
+    """One host core's share of the all-core baseline (a process of its own)."""
+    wl_name, seed_offset, steps = task
+    r, sample, secs = oracle_rate(wl_name, budget_s=1e9, steps=steps, seed_offset=seed_offset)
+    return r, sample, secs
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baselines(wl_name):
+    """The FP64 CPU oracle on the host: one core on a bounded sample; every core
+    at once, each on an independent sample of the same recipe (one process per
+    core, spawned); and the small uniform plasma in full on one core."""
+    import multiprocessing as mp
+    r, sample, secs = oracle_rate(wl_name, budget_s=25.0, steps=15)
+    ncores = os.cpu_count() or 1
+    out = {"value": r, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+           "sample": sample + " (%.1f s of CPU time)" % secs, "nproc": ncores, "cpu_model": cpu_model()}
+    try:
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(ncores) as pool:
+            res = pool.map(_oracle_worker, [(wl_name, 100 + i, 4) for i in range(ncores)])
+        wall = time.perf_counter() - t0
+        out["all_cores"] = {"value": sum(x[0] for x in res), "unit": "particle-updates/s", "cores": ncores,
+                            "sample": "%d independent samples at once (seeds offset 100..%d), each: %s"
+                                      % (ncores, 99 + ncores, res[0][1]),
+                            "wall_s": wall, "what": "sum of the per-process rates; one oracle process per core"}
+    except Exception as e:  # the all-core figure is optional context
+        out["all_cores"] = {"error": str(e)[:200]}
+    r1, s1, secs1 = oracle_rate("uniform32", budget_s=60.0, steps=50)
+    out["uniform32_full"] = {"value": r1, "unit": "particle-updates/s", "cores": 1,
+                             "sample": s1 + " (%.1f s)" % secs1}
+    return out
 
 
 def run_timeline(args):
@@ -675,13 +797,14 @@ def main():
             rates.append(r)
         secs = time.perf_counter() - t0
         v = statistics.median(rates)
+        wl_name = workload_name(args)
         line = {"metric": "particle-updates/s", "value": v, "unit": "particle-updates/s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "impl": "reference",
-                "config": {"workload": args.workload + " (bounded sample)", "sample": sample},
+                "config": {"workload": wl_name + " (bounded sample)", "sample": sample},
                 "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-                                 "sample": sample},
+                                 "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
                 "e2e": {"value": v, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -695,6 +818,17 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     res = run_ours(args, rank, world)
+    sec = None
+    if rank == 0 and args.secondary != "none" and args.secondary != args.workload:
+        import torch
+        torch.cuda.empty_cache()
+        sec = run_ours(args, 0, 1, wl=make_workload(args.secondary, args.scale), full=False)
+        sec = {"workload": sec["config"], "value": sec["value"], "unit": "particle-updates/s",
+               "ms_per_step": sec["ms_per_step"], "phase_ms_per_step": sec["phase_ms_per_step"],
+               "static_order": sec["static_order"], "mixed_precision": sec["mixed_precision"],
+               "fp32": sec["fp32"], "fdtd_cell_updates_per_s": sec["fdtd_cell_updates_per_s"],
+               "hbm_frac_fp64": BYTES_PER_PARTICLE * sec["_nparts"]
+               / (sec["phase_ms_per_step"]["particle"] / 1e3) / 1e9 / hbm_peak_gbs()}
     server = None
     if rank == 0 and not args.no_server:
         server = run_server(args)
@@ -703,19 +837,19 @@ def main():
         c3 = run_c3(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, sample, secs = oracle_rate(args.workload, budget_s=25.0, steps=15)
-        cpu = {"value": r, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-               "sample": sample + " (%.1f s of CPU time)" % secs}
+        cpu = cpu_baselines(args.workload)
     if rank == 0:
         line = {"metric": "particle-updates/s", "value": res["value"], "unit": "particle-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {1: "f64", 2: "float-float", 3: "f32"}[args.precision],
-                "data": "synthetic (seeded PCG64 workload recipe)", "config": res["config"], "clocks": res["clocks"], "e2e": res["e2e"],
+                "data": "synthetic (seeded PCG64 workload recipe)", "config": res["config"],
+                "clocks": res["clocks"], "e2e": res.get("e2e"),
                 "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "cpu_baseline": cpu,
-                "static_order": res["static_order"], "other_schedule": res["other_schedule"],
-                "cost_strategies": res["cost_strategies"], "mixed_precision": res["mixed_precision"],
-                "fp32": res["fp32"],
+                "static_order": res["static_order"], "cutting_vs_ordering": res.get("cutting_vs_ordering"),
+                "other_schedule": res.get("other_schedule"),
+                "cost_strategies": res.get("cost_strategies"), "mixed_precision": res["mixed_precision"],
+                "fp32": res["fp32"], "secondary": sec,
                 "batched_uneven_boxes": c3,
                 "cell_updates_per_s": res["cell_updates_per_s"],
                 "fdtd_cell_updates_per_s": res["fdtd_cell_updates_per_s"],
@@ -724,6 +858,12 @@ def main():
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def workload_name(args):
+    names = {"foil_at_scale": "foil512x512x1024", "foil256": "foil256x256x256", "uniform32": "uniform32",
+             "lognormal4096": "lognormal4096", "laser_ion_2d": "laser_ion_2d_1920"}
+    return names.get(args.workload, args.workload)
 
 
 if __name__ == "__main__":

@@ -148,7 +148,7 @@ pic_status pic_set_step(pic_sim* sim, int64_t step);
 pic_status pic_selftest_bounded_wait(pic_sim* sim, int64_t limit_ns);
 
 /* ---- load balancing (Sec. 2.2) ------------------------------------------- */
-enum { PIC_POLICY_KNAPSACK = 0, PIC_POLICY_SFC = 1 };
+enum { PIC_POLICY_KNAPSACK = 0, PIC_POLICY_SFC = 1, PIC_POLICY_BOX_ORDER = 2 };
 enum { PIC_COST_HEURISTIC = 0, PIC_COST_DEVICE_CLOCK = 1, PIC_COST_KERNEL_TIME = 2 };
 enum { PIC_LB_NONE = 0, PIC_LB_STATIC = 1, PIC_LB_DYNAMIC = 2 };
 enum { PIC_SCHED_LISTS = 0, PIC_SCHED_QUEUE = 1 };
@@ -160,7 +160,13 @@ enum { PIC_SCHED_LISTS = 0, PIC_SCHED_QUEUE = 1 };
  *   interval    steps between load-balancing calls (Sec. 3.3 scans 1..300).
  *   theta       required relative improvement of E to adopt a new mapping
  *               (E_new >= (1 + theta) E_old; Sec. 3.2 uses 0.10).
- *   policy      knapsack or Morton space-filling curve.
+ *   policy      knapsack or Morton space-filling curve (the paper's two
+ *               policies, Sec. 2.2), or BOX_ORDER: a control without cost
+ *               input -- the work units (boxes cut by cost as below) in
+ *               box-index order, contiguous equal-count pieces per worker,
+ *               pulled in that order by the queue schedule; it separates the
+ *               gain of cutting heavy boxes from that of cost-driven order.
+ *               pic_balance_compute accepts only the paper's two policies.
  *   cost        heuristic (w_p Np + w_c Nc per box), device clock (summed
  *               per-thread clock64 of the particle kernel, per box; the
  *               paper's GPU-clock strategy), or kernel time (summed
@@ -353,6 +359,18 @@ typedef struct {
 } pic_stats;
 pic_status pic_set_profiling(pic_sim* sim, int on);
 pic_status pic_get_stats(pic_sim* sim, pic_stats* out);
+
+/* Measures the FP64 fused multiply-add throughput of the current device, the
+ * denominator of the FP64 roofline of the particle kernel (GB300 executes
+ * FP64 at a small fraction of its FP32 rate, so the FP64 push is bound by this
+ * pipe rather than by HBM).  The paper has no counterpart: it reports no
+ * per-kernel rates.  Every SM runs 8 CTAs of 256 threads, each thread 8
+ * independent DFMA chains of `iters` iterations (1 <= iters <= 10^7); one
+ * warm-up launch, then the best of three launches timed with CUDA events on
+ * a private stream.  *tflops_out = 2 x 8 x iters x threads / seconds / 10^12.
+ * Allocates and frees a small device buffer.  Errors: PIC_EINVAL, PIC_ECUDA
+ * (message in pic_last_error(NULL)). */
+pic_status pic_probe_fp64_fma(int64_t iters, double* tflops_out);
 
 /* Releases all resources of the handle (also valid on a poisoned handle). */
 pic_status pic_destroy(pic_sim* sim);

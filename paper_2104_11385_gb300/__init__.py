@@ -5,7 +5,7 @@ package is the thin Python binding over it."""
 from . import _lib
 from ._lib import (BX, BY, BZ, COST_DEVICE_CLOCK, COST_HEURISTIC, COST_KERNEL_TIME, EX, EY, EZ, GATHER_ENERGY,
                    GATHER_MOMENTUM, JX, JY, JZ, LB_DYNAMIC,
-                   LB_NONE, LB_STATIC, POLICY_KNAPSACK, POLICY_SFC, RHO, SCHED_LISTS, SCHED_QUEUE,
+                   LB_NONE, LB_STATIC, POLICY_BOX_ORDER, POLICY_KNAPSACK, POLICY_SFC, RHO, SCHED_LISTS, SCHED_QUEUE,
                    PicError)
 from .sim import Simulation, balance_compute, lb_efficiency, lb_params
 

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA"
                 -5: "PIC_ESTATE", -6: "PIC_EUNSUPPORTED"}
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 BIN_NOALLOC_MAX_BOXES = 1 << 20  # PIC_BIN_NOALLOC_MAX_BOXES of include/pic_noalloc.h
-POLICY_KNAPSACK, POLICY_SFC = 0, 1
+POLICY_KNAPSACK, POLICY_SFC, POLICY_BOX_ORDER = 0, 1, 2
 COST_HEURISTIC, COST_DEVICE_CLOCK, COST_KERNEL_TIME = 0, 1, 2
 LB_NONE, LB_STATIC, LB_DYNAMIC = 0, 1, 2
 SCHED_LISTS, SCHED_QUEUE = 0, 1
@@ -122,6 +122,7 @@ SIGNATURES = [
     ("pic_autotune", _int, [_vp, _int, ctypes.POINTER(LaunchCfg)]),
     ("pic_set_profiling", _int, [_vp, _int]),
     ("pic_get_stats", _int, [_vp, ctypes.POINTER(Stats)]),
+    ("pic_probe_fp64_fma", _int, [_i64, _pd]),
     ("pic_destroy", _int, [_vp]),
     ("pic_last_error", ctypes.c_char_p, [_vp]),
     ("pic_server_create", _int, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),

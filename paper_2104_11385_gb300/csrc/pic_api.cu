@@ -231,7 +231,7 @@ int n_workers_for(const pic_sim* s, const pic_lb_params& p) {
 
 // builds the plan from units and their mapping
 void build_plan(pic_sim* s, const std::vector<pic::Unit>& units, const std::vector<int32_t>& assign,
-                int n_workers, int sched) {
+                int n_workers, int sched, bool box_order = false) {
     Plan& P = s->plan;
     P.units.clear();
     P.unit_cost.clear();
@@ -244,16 +244,18 @@ void build_plan(pic_sim* s, const std::vector<pic::Unit>& units, const std::vect
         // list w holds the units of worker w, heaviest first (ties: lower index)
         std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
             if (assign[a] != assign[b]) return assign[a] < assign[b];
-            return units[a].cost > units[b].cost;
+            return !box_order && units[a].cost > units[b].cost;
         });
         P.nlists = n_workers;
         P.list_off.assign(n_workers + 1, 0);
         for (int64_t i = 0; i < nu; ++i) P.list_off[assign[i] + 1]++;
         for (int w = 0; w < n_workers; ++w) P.list_off[w + 1] += P.list_off[w];
     } else {
-        // one queue, heaviest unit first (longest-processing-time order)
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int64_t a, int64_t b) { return units[a].cost > units[b].cost; });
+        // one queue, heaviest unit first (longest-processing-time order), or
+        // in box-index order for the box-order policy
+        if (!box_order)
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int64_t a, int64_t b) { return units[a].cost > units[b].cost; });
         P.nlists = 1;
         P.list_off = {0, (int32_t)nu};
     }
@@ -372,7 +374,7 @@ pic_lb_params default_lb() {
 pic_status validate_lb(pic_sim* s, const pic_lb_params* p) {
     if (!p) return fail(s, PIC_EINVAL, "null load-balancing parameters");
     if (p->mode < PIC_LB_NONE || p->mode > PIC_LB_DYNAMIC || p->interval < 1 || !(p->theta >= 0.0) ||
-        (p->policy != PIC_POLICY_KNAPSACK && p->policy != PIC_POLICY_SFC) ||
+        (p->policy != PIC_POLICY_KNAPSACK && p->policy != PIC_POLICY_SFC && p->policy != PIC_POLICY_BOX_ORDER) ||
         (p->cost != PIC_COST_HEURISTIC && p->cost != PIC_COST_DEVICE_CLOCK && p->cost != PIC_COST_KERNEL_TIME) ||
         !(p->cap_factor > 0.0) || p->n_workers < 0 || p->split < 0 ||
         (p->sched != PIC_SCHED_LISTS && p->sched != PIC_SCHED_QUEUE) || !std::isfinite(p->w_p) ||
@@ -398,7 +400,11 @@ void map_units(const pic_sim* s, const pic_lb_params& p, const std::vector<pic::
     uc.resize(units.size());
     for (size_t i = 0; i < units.size(); ++i) uc[i] = units[i].cost;
     assign.resize(units.size());
-    if (p.policy == PIC_POLICY_KNAPSACK) {
+    if (p.policy == PIC_POLICY_BOX_ORDER) {
+        // no cost input: units in box-index order, contiguous equal-count pieces
+        const int64_t nu = (int64_t)units.size();
+        for (int64_t i = 0; i < nu; ++i) assign[i] = (int32_t)((i * (int64_t)nw) / std::max<int64_t>(nu, 1));
+    } else if (p.policy == PIC_POLICY_KNAPSACK) {
         pic::knapsack(uc.data(), (int64_t)uc.size(), nw, p.cap_factor, assign.data());
     } else {
         std::vector<int32_t> ijk(3 * units.size());
@@ -425,7 +431,7 @@ pic_status rebalance(pic_sim* s, const pic_lb_params& p, double theta, pic_lb_re
     double e_new = pic::lb_efficiency(uc.data(), assign.data(), (int64_t)uc.size(), nw);
     bool adopted = pic::adopt(e_old, e_new, theta);
     if (adopted) {
-        build_plan(s, units, assign, nw, p.sched);
+        build_plan(s, units, assign, nw, p.sched, p.policy == PIC_POLICY_BOX_ORDER);
         TRY(upload_plan(s));
     }
     s->last_costs = costs;
@@ -528,7 +534,7 @@ pic_status replan(pic_sim* s) {
     std::vector<double> uc;
     std::vector<int32_t> assign;
     map_units(s, p, units, nw, uc, assign);  // the simulation's own policy
-    build_plan(s, units, assign, nw, p.sched);
+    build_plan(s, units, assign, nw, p.sched, p.policy == PIC_POLICY_BOX_ORDER);
     return upload_plan(s);
 }
 

@@ -89,7 +89,7 @@ __global__ void bin_scatter_kernel(BinGeom g, const double* __restrict__ x, cons
 int bin_grid(int64_t np) {
     int64_t b = (np + 255) / 256;
     if (b < 1) b = 1;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)pic_sm_count() * 16) b = (int64_t)pic_sm_count() * 16;
     return (int)b;
 }
 

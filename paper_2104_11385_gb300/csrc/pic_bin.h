@@ -22,5 +22,7 @@ pic_status pic_bin_validate(const pic_grid_desc* grid, const double* x, const do
 cudaError_t pic_bin_launch(const BinGeom& g, const double* x, const double* y, const double* z,
                            int64_t np, int64_t* box_off, int64_t* perm, int32_t* cursor,
                            cudaStream_t st);
+// streaming multiprocessors of the current device (defined in pic_particles.cu)
+int pic_sm_count();
 // records the message returned by pic_last_error(NULL) on this thread
 pic_status pic_record_error(pic_status st, const char* msg);

@@ -244,7 +244,7 @@ __global__ void fill_kernel(double* p, int64_t n, double v) {
 int blocks_for(int64_t n, int t) {
     int64_t b = (n + t - 1) / t;
     if (b < 1) b = 1;
-    if (b > 152 * 64) b = 152 * 64;
+    if (b > (int64_t)pic_sm_count() * 64) b = (int64_t)pic_sm_count() * 64;
     return (int)b;
 }
 

@@ -105,6 +105,10 @@ __host__ __device__ inline int64_t pidx(const SimDev& s, int i, int j, int k) {
     return ((int64_t)(k + s.g[2]) * s.pn[1] + (j + s.g[1])) * s.pn[0] + (i + s.g[0]);
 }
 
+// streaming multiprocessors of the current device, queried once per device
+// (pic_particles.cu): grid-stride launches cap their grids at a multiple of it
+int pic_sm_count();
+
 // ---- kernel launchers (defined in the .cu files) ----
 struct LaunchCfg {
     int threads;
@@ -159,7 +163,7 @@ cudaError_t pic_launch_sort_multi(SimDev* sims, const int* slots, int nslots, in
                                   cudaStream_t st);
 cudaError_t pic_launch_finish_multi(SimDev* sims, const int* slots, int nslots, const SchedDev* sched,
                                     cudaStream_t st);
-// dst[j] = src[(j * (2^31 - 1)) mod np] for the 7 SoA arrays (array `skip`
+// dst[j] = src[(j * (2^31 + 11)) mod np] for the 7 SoA arrays (array `skip`
 // left alone, -1 for none) and the ids: the one-time input-order scramble
 cudaError_t pic_launch_permute(double* const dst[7], const double* const src[7], int64_t* id_dst,
                                const int64_t* id_src, int64_t np, int skip, cudaStream_t st);

@@ -3,6 +3,7 @@
 // swap), end-of-step bookkeeping, initial keys, per-box counts, and the
 // dispatch of the particle kernel over its two arithmetic variants.
 #include <algorithm>
+#include <atomic>
 
 #include "pic_internal.h"
 #include "pic_sync.cuh"
@@ -175,6 +176,18 @@ __global__ void pic_scale_copy_kernel(const double* __restrict__ s, double* __re
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+int pic_sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 // particle kernel: dispatch on the arithmetic of the push
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
                                  const SchedDev* sched, SimDev* sims, cudaStream_t st) {
@@ -198,7 +211,7 @@ int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t sme
 static int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > (int64_t)pic_sm_count() * 32) b = (int64_t)pic_sm_count() * 32;
     return (int)b;
 }
 
@@ -255,8 +268,9 @@ cudaError_t pic_launch_box_counts(const SimDev* dsim, const SimDev& hsim, int64_
 // keeps the relative order of the particles that stay, so an input generated
 // cell by cell would keep a warp's 32 particles in one cell for the whole run,
 // all adding to the same J entries, and the shared-memory atomics would
-// serialise.  dst[j] = src[(j * P) mod np] with P = 2^31 - 1, a prime above
-// any species size, is a bijection that spreads consecutive inputs apart.
+// serialise.  dst[j] = src[(j * P) mod np] with P = 2^31 + 11, a prime above
+// any species size (np <= 2^31, so gcd(P, np) = 1), is a bijection that spreads
+// consecutive inputs apart; j * P < 2^63 needs no wider product.
 struct PermArrays {
     const double* src[7];
     double* dst[7];
@@ -265,7 +279,7 @@ struct PermArrays {
 };
 
 __global__ void pic_permute_kernel(PermArrays A, int64_t np, int skip) {
-    const uint64_t P = 2147483647ull;
+    const uint64_t P = 2147483659ull;  // 2^31 + 11, prime
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = (int64_t)(((uint64_t)j * P) % (uint64_t)np);
@@ -286,7 +300,7 @@ cudaError_t pic_launch_permute(double* const dst[7], const double* const src[7],
     }
     A.id_src = id_src;
     A.id_dst = id_dst;
-    const int64_t nb = std::min<int64_t>((np + 255) / 256, 152 * 32);
+    const int64_t nb = std::min<int64_t>((np + 255) / 256, (int64_t)pic_sm_count() * 32);
     pic_permute_kernel<<<(int)nb, 256, 0, st>>>(A, np, skip);
     return cudaGetLastError();
 }

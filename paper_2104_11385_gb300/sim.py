@@ -284,3 +284,11 @@ def bin_particles(dim, ncell, box, dx, x, y, z, box_off, perm, stream=None, fn="
     L.check(getattr(lib, fn)(ctypes.byref(g), ctypes.c_void_p(x.data_ptr()), yp,
                              ctypes.c_void_p(z.data_ptr()), int(x.numel()),
                              ctypes.c_void_p(box_off.data_ptr()), ctypes.c_void_p(perm.data_ptr())))
+
+
+def probe_fp64_fma(iters=20000) -> float:
+    """pic_probe_fp64_fma: measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    lib = L.load()
+    out = ctypes.c_double()
+    L.check(lib.pic_probe_fp64_fma(int(iters), ctypes.byref(out)))
+    return out.value

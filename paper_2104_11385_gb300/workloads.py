@@ -102,11 +102,16 @@ def foil(seed=2, n=(256, 256, 256), box=32, foil_z=(128, 136), ppc=64, density=3
     }
 
 
-def foil_at_scale(seed=5):
+def foil_at_scale(seed=5, scale=1):
     """The foil at scale: 512 x 512 x 1024 cells in 32^3 boxes, the foil 16
     cells thick (z in [512, 528)) at 64 ppc per species (536,870,912
-    particles); 2000 steps into the expansion, balancing every 20."""
-    wl = foil(seed=seed, n=(512, 512, 1024), box=32, foil_z=(512, 528), ppc=64)
+    particles); 2000 steps into the expansion, balancing every 20.  scale > 1
+    divides every extent (the foil's thickness, the boxes and the damping
+    layers too, down to 2 cells, 8 cells and 4 cells)."""
+    nx, nz = 512 // scale, 1024 // scale
+    t = max(2, 16 // scale)
+    wl = foil(seed=seed, n=(nx, nx, nz), box=max(8, 32 // scale), foil_z=(nz // 2, nz // 2 + t), ppc=64,
+              absorb=max(4, 16 // scale))
     wl["steps"], wl["lb_interval"] = 2000, 20
     return wl
 

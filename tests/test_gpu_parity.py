@@ -200,6 +200,8 @@ def test_cost_capture_switch():
     (pic.SCHED_LISTS, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
     (pic.SCHED_QUEUE, pic.POLICY_KNAPSACK, pic.COST_HEURISTIC),
     (pic.SCHED_LISTS, pic.POLICY_SFC, pic.COST_HEURISTIC),
+    (pic.SCHED_QUEUE, pic.POLICY_BOX_ORDER, pic.COST_DEVICE_CLOCK),
+    (pic.SCHED_LISTS, pic.POLICY_BOX_ORDER, pic.COST_HEURISTIC),
 ])
 def test_schedule_does_not_change_physics(sched, policy, cost):
     wl = workloads.random_plasma(77, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 1, nspecies=1,

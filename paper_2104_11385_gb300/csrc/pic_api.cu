@@ -470,7 +470,7 @@ pic_status enqueue_step(pic_sim* s, bool with_events) {
 }
 
 int count_kernels(const pic_sim* s) {
-    int k = (s->h.nsp > 0 ? 1 : 0) + 3 + (s->h.absorb > 0 ? 1 : 0) + 1 + 3 * s->h.nsp + 1;
+    int k = (s->h.nsp > 0 ? 1 : 0) + 1 + 3 + (s->h.absorb > 0 ? 1 : 0) + 1 + 3 * s->h.nsp + 1;
     return k;
 }
 
@@ -494,7 +494,7 @@ pic_status capture_graph(pic_sim* s) {
 }
 
 pic_status configure_launch(pic_sim* s) {
-    s->smem = pic_particle_smem_bytes(s->h.dim, s->h.order, s->h.T, s->threads);
+    s->smem = pic_particle_smem_bytes(s->h.dim, s->h.order, s->h.T, s->threads, s->prec);
     cudaDeviceProp prop;
     CU(s, cudaGetDeviceProperties(&prop, s->device));
     if (s->smem > prop.sharedMemPerBlockOptin)
@@ -569,7 +569,8 @@ int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, i
     int64_t pvol = 1, nboxes = 1, ntiles = 1;
     for (int a = 0; a < 3; ++a) {
         const bool act = !(g->dim == 2 && a == 1);
-        const int gw = act ? (a == 0 ? (g->shape_order == 3 ? PIC_GX + 1 : PIC_GX) : PIC_G) : 0;
+        const int gw = act ? (a == 0 ? (g->shape_order == 3 ? PIC_GX + 1 : PIC_GX)
+                                     : (g->shape_order >= 2 ? PIC_G + 1 : PIC_G)) : 0;
         pvol *= g->ncell[a] + 2 * gw;
         const int64_t nb = g->ncell[a] / std::max<int32_t>(1, g->box[a]);
         nboxes *= nb;
@@ -646,7 +647,10 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         h.n[a] = (int)g.ncell[a];
         h.nd[a] = (double)h.n[a];
         // x guard: even tile origin - E/B halo + guard must be even (TMA)
-        h.g[a] = act ? (a == 0 ? (g.shape_order == 3 ? PIC_GX + 1 : PIC_GX) : PIC_G) : 0;
+        // y, z: 2 guards, 3 for quadratic and cubic shapes, whose current
+        // windows reach 3 nodes above the domain
+        h.g[a] = act ? (a == 0 ? (g.shape_order == 3 ? PIC_GX + 1 : PIC_GX)
+                               : (g.shape_order >= 2 ? PIC_G + 1 : PIC_G)) : 0;
         h.pn[a] = h.n[a] + 2 * h.g[a];
         h.bsz[a] = g.box[a];
         h.nb[a] = h.n[a] / h.bsz[a];

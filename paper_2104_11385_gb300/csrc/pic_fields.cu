@@ -131,6 +131,33 @@ __global__ void damp_kernel(const SimDev* __restrict__ sims, const int* __restri
     }
 }
 
+// Current deposited in the guard cells of the padded J arrays (the particle
+// kernel's reductions reach up to 2 cells below and 3 above the domain) added
+// to its periodic image inside the domain.  Several guard cells share an image
+// (edges, corners), hence the reductions.  Guards of the FP32 variant, whose
+// tile flush wraps indices itself, hold zeros and are skipped.
+__global__ void fold_j_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
+    const SimDev& S = slot_sim(sims, slots);
+    const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
+    const int64_t pvol = (int64_t)px * py * pz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pvol;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int a = (int)(c % px);
+        int b = (int)((c / px) % py);
+        int e = (int)(c / ((int64_t)px * py));
+        int i = a - S.g[0], j = b - S.g[1], k = e - S.g[2];
+        bool inside = (i >= 0 && i < S.n[0]) && (j >= 0 && j < S.n[1]) && (k >= 0 && k < S.n[2]);
+        if (inside) continue;
+        const int64_t dst = pidx(S, ((i % S.n[0]) + S.n[0]) % S.n[0], ((j % S.n[1]) + S.n[1]) % S.n[1],
+                                 ((k % S.n[2]) + S.n[2]) % S.n[2]);
+#pragma unroll
+        for (int comp = 6; comp < 9; ++comp) {
+            const double v = S.F[comp][c];
+            if (v != 0.0) atomicAdd(S.F[comp] + dst, v);
+        }
+    }
+}
+
 // periodic images into the guard cells of components [c0, c0+nc)
 __global__ void guard_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots, int c0,
                              int nc) {
@@ -253,6 +280,8 @@ int blocks_for(int64_t n, int t) {
 cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t st) {
     const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
     const int nb = blocks_for(ncell, 256);
+    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
+    fold_j_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr);
     if (h.dim == 3) {
         b_half_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
         e_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
@@ -281,6 +310,7 @@ cudaError_t pic_launch_fields_multi(const SimDev* sims, const int* slots, int ns
                                     cudaStream_t st) {
     if (nslots <= 0) return cudaSuccess;
     const dim3 g(blocks_for(max_cells, 256) / 4 + 1, nslots);
+    fold_j_kernel<<<dim3(blocks_for(max_padded, 256) / 4 + 1, nslots), 256, 0, st>>>(sims, slots);
     if (dim == 3) {
         b_half_kernel<3><<<g, 256, 0, st>>>(sims, slots);
         e_kernel<3><<<g, 256, 0, st>>>(sims, slots);

@@ -3,11 +3,14 @@
 //
 // HBM layout of one simulation:
 //   fields  9 FP64 arrays (Ex Ey Ez Bx By Bz Jx Jy Jz), each padded by guard
-//           cells in every active direction (3 per side in x, 2 in y and z):
-//           dims (nx+6, ny+4, nz+4), x fastest (ny+4 -> 1 in 2D).  Guards of E and B hold the
-//           periodic images after every step, so a tile plus its halo is one
-//           rectangular TMA box; J guards stay zero (the deposit flush wraps
-//           indices itself).  J is one contiguous block of 3 arrays.
+//           cells in every active direction (3 per side in x, 4 for cubic
+//           shapes; 2 in y and z, 3 for quadratic and cubic): linear shapes
+//           give dims (nx+6, ny+4, nz+4), x fastest (ny+4 -> 1 in 2D).  Guards
+//           of E and B hold the periodic images after every step, so a tile
+//           plus its halo is one rectangular TMA box; J guards collect the
+//           current the particle kernel deposits beyond the domain, which the
+//           fold kernel adds to the periodic images.  J is one contiguous
+//           block of 3 arrays.
 //   particles per species, SoA of FP64 X Y Z (global cell units, X = x/dx),
 //           ux uy uz (u = gamma v), w, plus int64 id; double-buffered, sorted
 //           by tile (tiles numbered box-major, so each box is contiguous).
@@ -21,7 +24,7 @@
 
 #include "../../include/pic_api.h"
 
-#define PIC_G 2        // guard cells per side in y and z of the padded field arrays
+#define PIC_G 2        // guard cells per side in y and z of the padded field arrays (+1 for order >= 2)
 #define PIC_GX 3       // guard cells per side in x (4 for cubic shapes): a tile's TMA box
                        // starts 1 cell (2 for cubic) below an even tile origin and must
                        // start at an even padded x (x * 8 bytes a multiple of 16)
@@ -116,7 +119,8 @@ struct LaunchCfg {
     int minb;  // register budget variant of the particle kernel: 1 or 2 CTAs per SM
     int prec;  // arithmetic of the particle push: 0 FP64, 1 float-float
 };
-size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads);
+// dynamic shared memory of the particle kernel; prec 0 FP64, 1 float-float, 2 FP32
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, int prec);
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem);  // outside graph capture
 int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem,
                            int prec);  // resident CTAs per SM

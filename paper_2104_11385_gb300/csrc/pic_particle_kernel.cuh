@@ -6,9 +6,11 @@
 // pic_particle_kernel: persistent CTAs pull work units (a chunk of one box's
 // particles) from cost-ordered lists.  For every tile (sub-box) a unit touches,
 // the guard-extended E/B tile is staged into shared memory by TMA
-// (cp.async.bulk.tensor, local HBM only, no multicast), the current is
-// deposited into a shared-memory J tile with shared atomics and flushed
-// once per tile into the global J arrays.  Each thread brackets its particle
+// (cp.async.bulk.tensor, local HBM only, no multicast).  The current goes
+// straight into the guard-padded global J arrays as fire-and-forget FP64
+// reductions (red.global.add.f64, performed in L2; the FP64 and float-float
+// variants), or, in the FP32 variant, into a shared-memory FP32 J tile with
+// native shared atomics, flushed once per tile.  Each thread brackets its particle
 // loop with clock64(); the deltas are warp-reduced, summed in shared memory and
 // added once per unit to the box's cost -- the device-clock cost of
 // arXiv 2104.11385 Sec. 2.2 (Fig. 2a); thread 0 adds the unit's %globaltimer
@@ -434,10 +436,12 @@ struct SmemPlan {
     size_t bytes;
 };
 
-__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3]) {
+// jshared: the J tile lives in shared memory (FP32 variant); otherwise the
+// current goes to global memory and the J region is empty
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared) {
     SmemPlan p;
     p.eb_vol = ebs[0] * ebs[1] * ebs[2];
-    p.j_vol = js[0] * js[1] * js[2];
+    p.j_vol = jshared ? js[0] * js[1] * js[2] : 0;
     p.eb_stride = (p.eb_vol + 15) & ~15;
     p.j_stride = (p.j_vol + 1) & ~1;
     p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
@@ -465,23 +469,43 @@ __device__ void flush_j(const SimDev& S, const Tile& tl, const JT* __restrict__ 
 }
 
 
-// shared-memory J atomics: doubles for FP64 and float-float (a float-float
-// value is renormalised and merged to one double first), floats for FP32
-__device__ __forceinline__ void jadd(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void jadd(double* p, dd v) { atomicAdd(p, dd_to_norm(v)); }
-__device__ __forceinline__ void jadd(double* p, float v) { atomicAdd(p, f64_from(v)); }
+// Current accumulation.  FP64 and float-float add each contribution to the
+// global FP64 J with red.global.add.f64: the add runs in L2, nothing returns
+// to the SM, and no FP64 instruction is spent on it (a shared-memory FP64
+// atomic is a compare-and-swap loop whose retries each cost a full-warp FP64
+// add).  A float-float value is renormalised and merged to one double first.
+// The FP32 variant sums into a shared FP32 tile with native shared atomics.
+__device__ __forceinline__ void red_f64(double* p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void jadd(double* p, double v) { red_f64(p, v); }
+__device__ __forceinline__ void jadd(double* p, dd v) { red_f64(p, dd_to_norm(v)); }
 __device__ __forceinline__ void jadd(float* p, float v) { atomicAdd(p, v); }
 
-// element type of the shared J tile: FP32 for the FP32 variant (its own
-// tolerance covers the FP32 sums, and no FP64 compare-and-swap runs), FP64
-// otherwise; the flush adds each entry to the global FP64 J
+// element type of the J target: the global FP64 arrays (FP64, float-float),
+// the shared FP32 tile (FP32: its own tolerance covers the FP32 sums)
 template <class R>
 struct JAcc {
     using type = double;
+    static constexpr bool global = true;
 };
 template <>
 struct JAcc<float> {
     using type = float;
+    static constexpr bool global = false;
+};
+
+// Where a tile's current goes: base points at component 0 of local node
+// (-jlo, -jlo, -jlo) of the tile (jlo = S.jlo; y is 0 in 2D), cs is the
+// component stride, sy and sz the row and plane strides.  Shared tile: the
+// J tile's own extents.  Global: the padded J arrays, whose guard cells
+// (2 to 4 per side) hold the contributions that fall outside the domain until
+// the fold kernel adds them to their periodic images.
+template <class JT>
+struct JView {
+    JT* base;
+    int64_t cs;
+    int sy, sz;
 };
 
 // Esirkepov deposit of one particle into the shared J tile on windows of W
@@ -490,8 +514,7 @@ struct JAcc<float> {
 // weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3 = A_a A_b + DS_a DS_b / 12
 // with A = S0 + DS/2.  qw and vy in R; the prefactors -1/(dA dt) come from jf.
 template <class R, int DIM, int ORDER, int W>
-__device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type* __restrict__ sJ,
-                                        const SmemPlan& P,
+__device__ __forceinline__ bool deposit(const SimDev& S, const JView<typename JAcc<R>::type>& V,
                                         R qw, R vy, const R* jf, const Support<ORDER, R>& n0,
                                         const Support<ORDER, R>& n1, const Support<ORDER, R>& n2,
                                         const Support<ORDER, R>& m0, const Support<ORDER, R>& m1,
@@ -501,11 +524,11 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
     bool ok = make_window<ORDER, W, R>(n0, m0, wx) && make_window<ORDER, W, R>(n2, m2, wz);
     if (DIM == 3) ok = ok && make_window<ORDER, W, R>(n1, m1, wy);
     if (!ok) return false;
-    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    const int sy = V.sy, sz = V.sz, lo = S.jlo;
     using JT = typename JAcc<R>::type;
-    JT* Jx = sJ;
-    JT* Jy = sJ + P.j_stride;
-    JT* Jz = sJ + 2 * P.j_stride;
+    JT* Jx = V.base;
+    JT* Jy = V.base + V.cs;
+    JT* Jz = V.base + 2 * V.cs;
     const R half = A::c(0.5), k12 = A::c(1.0 / 12.0);
     R Ax[W], Az[W], Dx12[W], Dz12[W];
 #pragma unroll
@@ -524,12 +547,11 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
             Ay[l] = fma(half, wy.DS[l], wy.S0[l]);
             Dy12[l] = k12 * wy.DS[l];
         }
-        const int sxy = jx * jy;
-        JT* origin = sJ + ((wz.base + lo) * jy + (wy.base + lo)) * jx + (wx.base + lo);
+        JT* origin = V.base + (wz.base + lo) * sz + (wy.base + lo) * sy + (wx.base + lo);
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-            const int sa = pick3(a, 1, jx, sxy), sb = pick3(b, 1, jx, sxy), sc = pick3(c, 1, jx, sxy);
+            const int sa = pick3(a, 1, sy, sz), sb = pick3(b, 1, sy, sz), sc = pick3(c, 1, sy, sz);
             const R cf = qw * pick3(a, jf[0], jf[1], jf[2]);
             R Pf[W - 1], Ab[W], Ac[W], Db[W], Dc12[W];
             R acc = A::c(0.0);
@@ -544,7 +566,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
                 Ac[l] = c == 1 ? Ay[l] : Az[l];
                 Dc12[l] = c == 1 ? Dy12[l] : Dz12[l];
             }
-            JT* Ja = origin + a * P.j_stride;
+            JT* Ja = origin + a * V.cs;
 #pragma unroll 1
             for (int k = 0; k < W; ++k) {
                 R ack = Ac[0], dck = Dc12[0];
@@ -578,7 +600,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const R T = fma(Ay[j], Az[k], wy.DS[j] * Dz12[k]);
-                    JT* row = Jx + ((bz + k) * jy + (by + j)) * jx + bx;
+                    JT* row = Jx + (bz + k) * sz + (by + j) * sy + bx;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * T);
                 }
@@ -594,9 +616,9 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Az[k], wx.DS[i] * Dz12[k]);
-                    JT* col = Jy + ((bz + k) * jy + by) * jx + (bx + i);
+                    JT* col = Jy + (bz + k) * sz + by * sy + (bx + i);
 #pragma unroll
-                    for (int j = 0; j < W - 1; ++j) jadd(col + j * jx, Pf[j] * T);
+                    for (int j = 0; j < W - 1; ++j) jadd(col + j * sy, Pf[j] * T);
                 }
         }
         {
@@ -610,9 +632,9 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Ay[j], Dx12[i] * wy.DS[j]);
-                    JT* col = Jz + (bz * jy + (by + j)) * jx + (bx + i);
+                    JT* col = Jz + bz * sz + (by + j) * sy + (bx + i);
 #pragma unroll
-                    for (int k = 0; k < W - 1; ++k) jadd(col + k * jx * jy, Pf[k] * T);
+                    for (int k = 0; k < W - 1; ++k) jadd(col + k * sz, Pf[k] * T);
                 }
         }
     } else {
@@ -625,7 +647,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
             for (int l = 0; l < W - 1; ++l) { acc = acc + wx.DS[l]; Pf[l] = c * acc; }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                JT* row = Jx + (bz + k) * jx + bx;
+                JT* row = Jx + (bz + k) * sz + bx;
 #pragma unroll
                 for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * Az[k]);
             }
@@ -638,9 +660,9 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
             for (int k = 0; k < W - 1; ++k) { acc = acc + wz.DS[k]; Pf[k] = c * acc; }
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                JT* col = Jz + bz * jx + (bx + i);
+                JT* col = Jz + bz * sz + (bx + i);
 #pragma unroll
-                for (int k = 0; k < W - 1; ++k) jadd(col + k * jx, Pf[k] * Ax[i]);
+                for (int k = 0; k < W - 1; ++k) jadd(col + k * sz, Pf[k] * Ax[i]);
             }
         }
         {  // out-of-plane Jy = q w vy / (dx dz) * (Ax Az + DSx DSz / 12)
@@ -649,7 +671,7 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
             for (int k = 0; k < W; ++k)
 #pragma unroll
                 for (int i = 0; i < W; ++i)
-                    jadd(Jy + (bz + k) * jx + (bx + i), c * fma(Ax[i], Az[k], Dx12[i] * wz.DS[k]));
+                    jadd(Jy + (bz + k) * sz + (bx + i), c * fma(Ax[i], Az[k], Dx12[i] * wz.DS[k]));
         }
     }
     return true;
@@ -661,16 +683,16 @@ __device__ __forceinline__ bool deposit(const SimDev& S, typename JAcc<R>::type*
 // A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
 // deposit<R, DIM, 1, 2>, with fewer instructions.
 template <class R, int DIM>
-__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, typename JAcc<R>::type* __restrict__ sJ,
-                                                   const SmemPlan& P, R qw, R vy, const R* jf,
+__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+                                                   R qw, R vy, const R* jf,
                                                    const Support<1, R>* n, const Support<1, R>* m) {
     using A = Arith<R>;
     const R k12 = A::c(1.0 / 12.0), half = A::c(0.5), one = A::c(1.0);
-    const int jx = S.js[0], jy = S.js[1], lo = S.jlo;
+    const int sy = V.sy, sz = V.sz, lo = S.jlo;
     using JT = typename JAcc<R>::type;
-    JT* Jx = sJ;
-    JT* Jy = sJ + P.j_stride;
-    JT* Jz = sJ + 2 * P.j_stride;
+    JT* Jx = V.base;
+    JT* Jy = V.base + V.cs;
+    JT* Jz = V.base + 2 * V.cs;
     const R dx = m[0].w[1] - n[0].w[1], dz = m[2].w[1] - n[2].w[1];
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
@@ -681,76 +703,83 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, typename JAc
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
         const int by = n[1].s + lo;
-        const int sxy = jx * jy;
-        JT* origin = sJ + (bz * jy + by) * jx + bx;
+        JT* origin = V.base + bz * sz + by * sy + bx;
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-            const int sb = pick3(b, 1, jx, sxy), sc = pick3(c, 1, jx, sxy);
+            const int sb = pick3(b, 1, sy, sz), sc = pick3(c, 1, sy, sz);
             const R db = b == 0 ? dx : dy, dc = c == 1 ? dy : dz;
             const R mb = b == 0 ? mx : my, mc = c == 1 ? my : mz;
             const R ab = b == 0 ? ax0 : ay0, ac = c == 1 ? ay0 : az0;
             const R e = (db * dc) * k12;
             const R pf = -((qw * pick3(a, jf[0], jf[1], jf[2])) * pick3(a, dx, dy, dz));
-            JT* r = origin + a * P.j_stride;
+            JT* r = origin + a * V.cs;
             jadd(r, pf * fma(ab, ac, e));
             jadd(r + sb, pf * fma(mb, ac, -e));
             jadd(r + sc, pf * fma(ab, mc, -e));
             jadd(r + sb + sc, pf * fma(mb, mc, e));
         }
     } else if constexpr (DIM == 3) {
+        // value of node (b, c) of current a: pf_a (A_b A_c + s d_b d_c / 12),
+        // s = +1 on the diagonal nodes, -1 off it, pf_a = -q w jf_a d_a; with
+        // pe_a = pf_a d_b d_c / 12 = -q w jf_a (d_x d_y d_z / 12) and the node
+        // weights (1 - m, m) each value is one FMA of pf_a A_b against A_c
         const R dy = m[1].w[1] - n[1].w[1];
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
         const int by = n[1].s + lo;
+        const R d3 = (dx * dy) * (dz * k12);
         {   // Jx at (bx, by + j, bz + k)
-            const R e = (dy * dz) * k12;
-            const R pf = -((qw * jf[0]) * dx);
-            JT* r = Jx + (bz * jy + by) * jx + bx;
-            jadd(r, pf * fma(ay0, az0, e));
-            jadd(r + jx, pf * fma(my, az0, -e));
-            jadd(r + jx * jy, pf * fma(ay0, mz, -e));
-            jadd(r + jx * jy + jx, pf * fma(my, mz, e));
+            const R q = qw * jf[0];
+            const R pf = -(q * dx), pe = -(q * d3);
+            const R p1 = pf * my, p0 = pf - p1;
+            JT* r = Jx + bz * sz + by * sy + bx;
+            jadd(r, fma(p0, az0, pe));
+            jadd(r + sy, fma(p1, az0, -pe));
+            jadd(r + sz, fma(p0, mz, -pe));
+            jadd(r + sz + sy, fma(p1, mz, pe));
         }
         {   // Jy at (bx + i, by, bz + k)
-            const R e = (dx * dz) * k12;
-            const R pf = -((qw * jf[1]) * dy);
-            JT* r = Jy + (bz * jy + by) * jx + bx;
-            jadd(r, pf * fma(ax0, az0, e));
-            jadd(r + 1, pf * fma(mx, az0, -e));
-            jadd(r + jx * jy, pf * fma(ax0, mz, -e));
-            jadd(r + jx * jy + 1, pf * fma(mx, mz, e));
+            const R q = qw * jf[1];
+            const R pf = -(q * dy), pe = -(q * d3);
+            const R p1 = pf * mx, p0 = pf - p1;
+            JT* r = Jy + bz * sz + by * sy + bx;
+            jadd(r, fma(p0, az0, pe));
+            jadd(r + 1, fma(p1, az0, -pe));
+            jadd(r + sz, fma(p0, mz, -pe));
+            jadd(r + sz + 1, fma(p1, mz, pe));
         }
         {   // Jz at (bx + i, by + j, bz)
-            const R e = (dx * dy) * k12;
-            const R pf = -((qw * jf[2]) * dz);
-            JT* r = Jz + (bz * jy + by) * jx + bx;
-            jadd(r, pf * fma(ax0, ay0, e));
-            jadd(r + 1, pf * fma(mx, ay0, -e));
-            jadd(r + jx, pf * fma(ax0, my, -e));
-            jadd(r + jx + 1, pf * fma(mx, my, e));
+            const R q = qw * jf[2];
+            const R pf = -(q * dz), pe = -(q * d3);
+            const R p1 = pf * mx, p0 = pf - p1;
+            JT* r = Jz + bz * sz + by * sy + bx;
+            jadd(r, fma(p0, ay0, pe));
+            jadd(r + 1, fma(p1, ay0, -pe));
+            jadd(r + sy, fma(p0, my, -pe));
+            jadd(r + sy + 1, fma(p1, my, pe));
         }
     } else {
         {   // Jx at (bx, bz + k): -(q w/(dz dt)) DSx A_z
             const R pf = -((qw * jf[0]) * dx);
-            JT* r = Jx + bz * jx + bx;
+            JT* r = Jx + bz * sz + bx;
             jadd(r, pf * az0);
-            jadd(r + jx, pf * mz);
+            jadd(r + sz, pf * mz);
         }
         {   // Jz at (bx + i, bz)
             const R pf = -((qw * jf[2]) * dz);
-            JT* r = Jz + bz * jx + bx;
+            JT* r = Jz + bz * sz + bx;
             jadd(r, pf * ax0);
             jadd(r + 1, pf * mx);
         }
         {   // out-of-plane Jy at (bx + i, bz + k)
             const R e = (dx * dz) * k12;
             const R c = qw * vy * jf[1];
-            JT* r = Jy + bz * jx + bx;
+            JT* r = Jy + bz * sz + bx;
             jadd(r, c * fma(ax0, az0, e));
             jadd(r + 1, c * fma(mx, az0, -e));
-            jadd(r + jx, c * fma(ax0, mz, -e));
-            jadd(r + jx + 1, c * fma(mx, mz, e));
+            jadd(r + sz, c * fma(ax0, mz, -e));
+            jadd(r + sz + 1, c * fma(mx, mz, e));
         }
     }
 }
@@ -760,7 +789,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, typename JAc
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
 template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
-                                         const R* __restrict__ sEB, typename JAcc<R>::type* __restrict__ sJ,
+                                         const R* __restrict__ sEB, const JView<typename JAcc<R>::type>& V,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                          const R* jf, const R* dtd, R kq, R qs, int64_t p, int32_t* err) {
     using A = Arith<R>;
@@ -831,9 +860,9 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
     if (same) {
         if constexpr (ORDER == 1)
-            deposit_lin_incell<R, DIM>(S, sJ, P, qw, v1, jf, nd, mv);
+            deposit_lin_incell<R, DIM>(S, V, qw, v1, jf, nd, mv);
         else
-            deposit<R, DIM, ORDER, ORDER + 1>(S, sJ, P, qw, v1, jf, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
+            deposit<R, DIM, ORDER, ORDER + 1>(S, V, qw, v1, jf, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
     } else {
         // the ring never holds more than 31 + 32 entries: the warp drains 32
         // whenever 32 are waiting
@@ -884,10 +913,14 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
 
 // A warp deposits n <= 32 queued (cell-crossing) particles of its ring,
 // starting at slot head, on the ORDER + 2 window: lane i takes entry head + i.
+// Supports are taken relative to the origin of tile tl and the view V is that
+// tile's; with the global J target any tile gives the same global nodes (the
+// entries hold global positions), so rings then drain across tile changes.
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, typename JAcc<R>::type* __restrict__ sJ,
+__device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl,
+                                           const JView<typename JAcc<R>::type>& V,
                                            const double* __restrict__ sQw, unsigned head, unsigned n,
-                                           const SmemPlan& P, const R* jf, int32_t* err) {
+                                           const R* jf, int32_t* err) {
     using A = Arith<R>;
     const unsigned lane = threadIdx.x & 31u;
     if (lane >= n) return;
@@ -909,7 +942,7 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, type
         nd[1].w[0] = A::c(1.0);
         mv[1] = nd[1];
     }
-    if (!deposit<R, DIM, ORDER, ORDER + 2>(S, sJ, P, A::from(qw), A::from(vy), jf, nd[0], nd[1], nd[2],
+    if (!deposit<R, DIM, ORDER, ORDER + 2>(S, V, A::from(qw), A::from(vy), jf, nd[0], nd[1], nd[2],
                                            mv[0], mv[1], mv[2]))
         atomicOr(err, PIC_DERR_BOUNDS);
 }
@@ -919,20 +952,40 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl, type
 // (about 5 % of the kernel); FP64 is indifferent and inlines it, as does FP32
 template <class R, int DIM, int ORDER>
 __device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl,
-                                                 typename JAcc<R>::type* __restrict__ sJ,
+                                                 const JView<typename JAcc<R>::type>& V,
                                                  const double* __restrict__ sQw, unsigned head, unsigned n,
-                                                 const SmemPlan& P, const R* jf, int32_t* err) {
-    drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
+                                                 const R* jf, int32_t* err) {
+    drain_warp<R, DIM, ORDER>(S, tl, V, sQw, head, n, jf, err);
 }
 
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, typename JAcc<R>::type* __restrict__ sJ,
+__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, const JView<typename JAcc<R>::type>& V,
                                       const double* __restrict__ sQw, unsigned head, unsigned n,
-                                      const SmemPlan& P, const R* jf, int32_t* err) {
+                                      const R* jf, int32_t* err) {
     if constexpr (!std::is_same<R, dd>::value)
-        drain_warp<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
+        drain_warp<R, DIM, ORDER>(S, tl, V, sQw, head, n, jf, err);
     else
-        drain_warp_outlined<R, DIM, ORDER>(S, tl, sJ, sQw, head, n, P, jf, err);
+        drain_warp_outlined<R, DIM, ORDER>(S, tl, V, sQw, head, n, jf, err);
+}
+
+// the J view of tile tl: the shared FP32 tile, or the global padded arrays
+template <class JT>
+__device__ __forceinline__ JView<JT> j_view(const SimDev& S, const Tile& tl, JT* sJ, const SmemPlan& P) {
+    JView<JT> v;
+    if constexpr (JAcc<JT>::global) {
+        const int lo = S.jlo;
+        v.base = reinterpret_cast<JT*>(S.F[6]) +
+                 pidx(S, tl.o[0] - lo, S.dim == 3 ? tl.o[1] - lo : 0, tl.o[2] - lo);
+        v.cs = (int64_t)S.pn[0] * S.pn[1] * S.pn[2];
+        v.sy = S.pn[0];
+        v.sz = S.pn[0] * S.pn[1];
+    } else {
+        v.base = sJ;
+        v.cs = P.j_stride;
+        v.sy = S.js[0];
+        v.sz = S.js[0] * S.js[1];
+    }
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -941,16 +994,34 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// the simulation's constants in the push arithmetic R
+template <class R, int DIM>
+struct SimConsts {
+    R jf[3], dtd[3];
+    __device__ __forceinline__ explicit SimConsts(const SimDev& S) {
+        using A = Arith<R>;
+        jf[0] = A::from(S.jfac[0]);
+        jf[1] = A::from(DIM == 3 ? S.jfac[1] : S.jyfac2d);
+        jf[2] = A::from(S.jfac[2]);
+        dtd[0] = A::from(S.dtd[0]);
+        dtd[1] = A::from(S.dtd[1]);
+        dtd[2] = A::from(S.dtd[2]);
+    }
+};
+
 // MINB = resident CTAs per SM the register allocation is sized for (1: up to
 // 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM).
 // PREC = arithmetic of the particle push: 0 FP64, 1 float-float, 2 FP32 (storage,
-// positions and index math stay FP64 in all three; the shared J tile is FP64
-// except in the FP32 variant, whose tile sums in FP32).
+// positions and index math stay FP64 in all three; the current goes to the
+// global FP64 J by L2 reductions, except in the FP32 variant, whose shared
+// tile sums in FP32).
 template <int DIM, int ORDER, int MINB, int PREC>
 __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                               SimDev* __restrict__ sims) {
     using R = typename std::conditional<PREC == 1, dd, typename std::conditional<PREC == 2, float, double>::type>::type;
     using A = Arith<R>;
+    using JT = typename JAcc<R>::type;
+    constexpr bool GJ = JAcc<R>::global;
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -976,6 +1047,26 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     cur.sim = -1;
     cur.t = -1;
     int visited = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // global J target: a warp's ring of cell-crossing particles outlives tile
+    // changes; it is drained when the simulation changes (rings hold one
+    // simulation's particles, at that simulation's queue offset) and at the end
+    auto drain_ring = [&](const SimDev& CS) {
+        if constexpr (GJ) {
+            const unsigned head = s_qhead[warp], tail = s_qtail[warp];
+            if (tail != head) {
+                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false);
+                const SimConsts<R, DIM> K(CS);
+                double* sQw = smem + 6 * CP.eb_stride + warp * (QFields<DIM>::n * WQ);
+                drain<R, DIM, ORDER>(CS, cur, j_view<JT>(CS, cur, nullptr, CP), sQw, head, tail - head, K.jf,
+                                     sd->err);
+                __syncwarp();
+                if (lane == 0) s_qhead[warp] = tail;
+                __syncwarp();
+            }
+        }
+    };
 
     while (true) {
         if (threadIdx.x == 0) {
@@ -998,16 +1089,13 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         const SimDev& S = sims[unit.sim];
         const bool cap_clk = (S.capture & 1) != 0, cap_time = (S.capture & 2) != 0;
         const uint64_t t_unit0 = (threadIdx.x == 0 && cap_time) ? globaltimer() : 0ull;
-        const SmemPlan P = smem_plan(S.ebs, S.js);
+        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ);
         double* sEBd = smem;
         const R* sEB = reinterpret_cast<const R*>(smem);
-        double* sJd = smem + 6 * P.eb_stride;  // J region (doubles); the queues follow it
-        using JT = typename JAcc<R>::type;
+        double* sJd = smem + 6 * P.eb_stride;  // J tile (FP32 variant only); the rings follow it
         JT* sJ = reinterpret_cast<JT*>(sJd);
         unsigned long long my_clk = 0ull;
-        // the simulation's constants in R
-        const R jf[3] = {A::from(S.jfac[0]), A::from(DIM == 3 ? S.jfac[1] : S.jyfac2d), A::from(S.jfac[2])};
-        const R dtd[3] = {A::from(S.dtd[0]), A::from(S.dtd[1]), A::from(S.dtd[2])};
+        const SimConsts<R, DIM> K(S);
 
         for (int spi = 0; spi < S.nsp; ++spi) {
             const SpeciesDev& sp = S.sp[spi];
@@ -1023,12 +1111,15 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 const int64_t s0 = max(sp.off[t], r0), s1 = min(sp.off[t + 1], r1);
                 if (s0 >= s1) continue;
                 if (t != cur.t || unit.sim != cur.sim) {
+                    if (GJ && cur.t >= 0 && unit.sim != cur.sim) drain_ring(sims[cur.sim]);
                     __syncthreads();
-                    if (cur.t >= 0) {
-                        const SimDev& CS = sims[cur.sim];
-                        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
-                        flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const typename JAcc<R>::type*>(smem + 6 * CP.eb_stride), CP);
-                        __syncthreads();
+                    if constexpr (!GJ) {
+                        if (cur.t >= 0) {
+                            const SimDev& CS = sims[cur.sim];
+                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true);
+                            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride), CP);
+                            __syncthreads();
+                        }
                     }
                     cur.sim = unit.sim;
                     cur.t = t;
@@ -1044,7 +1135,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         for (int c = 0; c < 6; ++c)
                             tma_load_3d(sEBd + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
                     }
-                    for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJd[i] = 0.0;
+                    if constexpr (!GJ)
+                        for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJd[i] = 0.0;
                     bool ok = mbar_wait_bounded(&bar, phase);
                     phase ^= 1u;
                     if (!ok) {
@@ -1073,17 +1165,17 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         // (a round's floats cover doubles below its own end)
                         float* sEBf = reinterpret_cast<float*>(sEBd);
                         const int ntot = 6 * P.eb_stride;
-                        constexpr int K = 4;
-                        for (int base = 0; base < ntot; base += K * blockDim.x) {
-                            double v[K];
+                        constexpr int KR = 4;
+                        for (int base = 0; base < ntot; base += KR * blockDim.x) {
+                            double v[KR];
 #pragma unroll
-                            for (int q = 0; q < K; ++q) {
+                            for (int q = 0; q < KR; ++q) {
                                 const int i = base + q * blockDim.x + threadIdx.x;
                                 v[q] = i < ntot ? sEBd[i] : 0.0;
                             }
                             __syncthreads();
 #pragma unroll
-                            for (int q = 0; q < K; ++q) {
+                            for (int q = 0; q < KR; ++q) {
                                 const int i = base + q * blockDim.x + threadIdx.x;
                                 if (i < ntot) sEBf[i] = f32_from(v[q]);
                             }
@@ -1094,31 +1186,34 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 const unsigned long long c0 = cap_clk ? clock64() : 0ull;
                 {
                     // per-warp loop: no CTA barrier until the tile changes
-                    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                    const JView<JT> V = j_view<JT>(S, cur, sJ, P);
                     double* sQw = sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
                     volatile unsigned* vtail = s_qtail + warp;
                     for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
                         const int64_t p = p0 + lane;
                         if (p < s1)
-                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, sJ, sQw, s_qtail + warp, P, jf, dtd, kq, qs, p,
-                                                    sd->err);
+                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq, qs,
+                                                    p, sd->err);
                         __syncwarp();
                         const unsigned head = s_qhead[warp], tail = *vtail;
                         if (tail - head >= 32u) {
-                            drain<R, DIM, ORDER>(S, cur, sJ, sQw, head, 32u, P, jf, sd->err);
+                            drain<R, DIM, ORDER>(S, cur, V, sQw, head, 32u, K.jf, sd->err);
                             __syncwarp();
                             if (lane == 0) s_qhead[warp] = head + 32u;
                             __syncwarp();
                         }
                     }
                     __syncwarp();
-                    const unsigned head = s_qhead[warp], tail = *vtail;
-                    if (tail != head) {
-                        drain<R, DIM, ORDER>(S, cur, sJ, sQw, head, tail - head, P, jf, sd->err);
+                    if constexpr (!GJ) {
+                        // the shared tile is flushed at the tile change: drain the ring now
+                        const unsigned head = s_qhead[warp], tail = *vtail;
+                        if (tail != head) {
+                            drain<R, DIM, ORDER>(S, cur, V, sQw, head, tail - head, K.jf, sd->err);
+                            __syncwarp();
+                            if (lane == 0) s_qhead[warp] = tail;
+                        }
                         __syncwarp();
-                        if (lane == 0) s_qhead[warp] = tail;
                     }
-                    __syncwarp();
                 }
                 if (cap_clk) my_clk += clock64() - c0;
             }
@@ -1139,10 +1234,14 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         }
     }
     if (cur.t >= 0) {
-        __syncthreads();
-        const SimDev& CS = sims[cur.sim];
-        const SmemPlan CP = smem_plan(CS.ebs, CS.js);
-        flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const typename JAcc<R>::type*>(smem + 6 * CP.eb_stride), CP);
+        if constexpr (GJ) {
+            drain_ring(sims[cur.sim]);
+        } else {
+            __syncthreads();
+            const SimDev& CS = sims[cur.sim];
+            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true);
+            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride), CP);
+        }
     }
 }
 

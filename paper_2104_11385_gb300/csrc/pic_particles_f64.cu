@@ -19,7 +19,7 @@ int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t 
     return 0;
 }
 
-size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads) {
+size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, int prec) {
     int ebs[3], js[3];
     for (int a = 0; a < 3; ++a) {
         bool act = !(dim == 2 && a == 1);
@@ -27,7 +27,8 @@ size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads) 
         js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
     }
     if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
-    // tiles + one crossing ring per warp + alignment slack of the dynamic base
+    // tiles (the J tile only for the FP32 variant, prec 2) + one crossing ring
+    // per warp + alignment slack of the dynamic base
     const int qf = dim == 3 ? QFields<3>::n : QFields<2>::n;
-    return smem_plan(ebs, js).bytes + (size_t)(threads / 32) * qf * WQ * sizeof(double) + 128;
+    return smem_plan(ebs, js, prec == 2).bytes + (size_t)(threads / 32) * qf * WQ * sizeof(double) + 128;
 }

@@ -219,7 +219,7 @@ pic_status admit(pic_server* s, Request& r, int slot) {
     s->max_padded = std::max(s->max_padded, pvol);
     s->max_cells = std::max(s->max_cells, (int64_t)mirror.n[0] * mirror.n[1] * mirror.n[2]);
     for (int i = 0; i < mirror.nsp; ++i) s->max_cap = std::max(s->max_cap, mirror.sp[i].cap);
-    s->smem = std::max(s->smem, pic_particle_smem_bytes(mirror.dim, mirror.order, mirror.T, s->threads));
+    s->smem = std::max(s->smem, pic_particle_smem_bytes(mirror.dim, mirror.order, mirror.T, s->threads, 0));
     return PIC_OK;
 }
 
@@ -423,7 +423,7 @@ pic_status pic_server_tick(pic_server* s, int* n_active, int* n_pending) {
                             "device-side check failed (error word " + std::to_string(e) + ")");
         s->stats.ticks++;
         s->stats.particle_launches++;
-        s->stats.kernels += 1 + 1 + 4 + 3 + 1;
+        s->stats.kernels += 1 + 1 + 5 + 3 + 1;
         const double t = now_s();
         for (int sl : s->active_slots) {
             Request& r = s->reqs[s->slot_owner[sl]];

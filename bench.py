@@ -56,7 +56,7 @@ BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 # captured.
 TRAFFIC_CAPTURE = {"bytes_per_particle": (506.900992e6 + 413.934592e6) / 8388608, "dim": 3, "order": 1,
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
-                               "paper_2104_11385_gb300/csrc/pic_particles_f64.cu",
+                               "paper_2104_11385_gb300/csrc/pic_particles_f64_3d.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h",
                                "paper_2104_11385_gb300/csrc/pic_sync.cuh"),
@@ -317,7 +317,7 @@ def run_ours(args, rank, world, wl=None, full=True):
     st = profiled(sim, args.steps)
     kernels_per_step = st["launches"] / max(st["steps"], 1)
     release(sim)
-    tkw = {k: tuned[k] for k in ("threads", "ctas_per_sm", "split")}
+    tkw = {k: tuned[k] for k in ("threads", "ctas_per_sm", "split", "tile", "ppt")}
 
     # ---- reduced-precision variants (float-float push; FP32 push with FP32 tile sums)
     variants = {}
@@ -348,7 +348,8 @@ def run_ours(args, rank, world, wl=None, full=True):
 
     # ---- static box order (no load balancing: the fixed starting mapping)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)
-    sim.set_launch(threads=tuned["threads"], ctas_per_sm=tuned["ctas_per_sm"], precision=args.precision)
+    sim.set_launch(threads=tuned["threads"], ctas_per_sm=tuned["ctas_per_sm"], tile=tuned["tile"], ppt=tuned["ppt"],
+                   precision=args.precision)
     sim.step(1 + min(args.warmup, 2))
     ks = max(1, args.static_steps)
     ms_static = timed(sim, ks)

@@ -325,7 +325,19 @@ pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const d
  *   threads       threads per CTA (a multiple of 32, at most 256).
  *   ctas_per_sm   persistent CTAs per SM (1 or 2; 2 selects the kernel
  *                 variant compiled for 128 registers; capped by occupancy).
- *   split         target work units per worker when boxes are cut.
+ *   split         target work units per worker when boxes are cut (the
+ *                 number of CTAs that share a heavy box).
+ *   tile          cells per tile edge in every active direction: the unit of
+ *                 field staging (a guard-extended E/B tile per tile in shared
+ *                 memory) and of the particle sort.  Even, dividing every box
+ *                 extent, at least 4, and small enough for its staged tile to
+ *                 fit in shared memory.  The default is the largest even
+ *                 divisor of the box up to 8 (3D) or 16 (2D).  A change
+ *                 re-tiles the simulation: tile maps, sort arrays and every
+ *                 species' order are rebuilt (synchronises).
+ *   ppt           particles per thread per loop iteration (1 or 2): the HBM
+ *                 loads of that many particles are issued before the first
+ *                 of them is pushed.
  *   precision     arithmetic of the particle push: 1 FP64 (default);
  *                 2 float-float (pairs of FP32 with error-free
  *                 transformations, ~48-bit significand) for gather, Boris and
@@ -338,15 +350,20 @@ pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const d
  *                 FP64 one); 0 keeps the current setting.  The autotuner
  *                 never changes it. */
 typedef struct {
-    int threads, ctas_per_sm, split, precision;
+    int threads, ctas_per_sm, split, precision, tile, ppt;
 } pic_launch_cfg;
 pic_status pic_set_launch(pic_sim* sim, const pic_launch_cfg* cfg);
 pic_status pic_get_launch(const pic_sim* sim, pic_launch_cfg* cfg);
 
-/* Autotuner: times each candidate launch configuration on real steps of this
+/* Autotuner: times candidate launch configurations on real steps of this
  * simulation (steps_per_candidate steps each, after one warm-up step; the
- * steps advance the simulation) and keeps the fastest.  *best receives it
- * (nullable).  Synchronises. */
+ * steps advance the simulation) and keeps the fastest.  The search runs by
+ * coordinates, each stage keeping the best of the previous ones: tile size
+ * (the even divisors of the box from 4 up to 8 in 3D, 32 in 2D, that fit in
+ * shared memory) x particles per thread {1, 2}; then threads per CTA
+ * {128, 256} x CTAs per SM {1, 2}; then work units per worker {4, 16, 64}
+ * (only when load balancing cuts boxes).  The precision is never changed.
+ * *best receives the result (nullable).  Synchronises. */
 pic_status pic_autotune(pic_sim* sim, int steps_per_candidate, pic_launch_cfg* best);
 
 /* Timing of the last pic_step call, from CUDA events recorded on the

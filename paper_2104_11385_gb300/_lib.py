@@ -53,7 +53,8 @@ class LBResult(ctypes.Structure):
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("threads", _int), ("ctas_per_sm", _int), ("split", _int), ("precision", _int)]
+    _fields_ = [("threads", _int), ("ctas_per_sm", _int), ("split", _int), ("precision", _int), ("tile", _int),
+                ("ppt", _int)]
 
 
 PREC_FP64, PREC_FLOAT_FLOAT, PREC_FP32 = 1, 2, 3

@@ -82,7 +82,9 @@ struct pic_sim {
     int ctas = 0;
     int minb = 1;
     int prec = 0;  // 0 FP64, 1 float-float, 2 FP32 particle push
+    int ppt = 1;   // particles per thread per loop iteration
     size_t smem = 0;
+    int64_t tiles_cap[PIC_MAXSP] = {0, 0, 0, 0};  // sort arrays allocated for this many tiles
     // load balancing
     pic_lb_params lb{};
     bool lb_set = false;
@@ -213,6 +215,49 @@ int largest_even_divisor_le(int b, int cap) {
     for (int t = std::min(b, cap); t >= 2; --t)
         if (b % t == 0 && t % 2 == 0) return t;
     return 0;
+}
+
+// tile extents t[a] (cells per tile edge, 1 for the inactive y of 2D runs) and
+// everything derived from them: tiles per box, tile count, staged E/B and J
+// tile extents
+void set_tiling(SimDev& h, const int t[3]) {
+    for (int a = 0; a < 3; ++a) {
+        const bool act = !(h.dim == 2 && a == 1);
+        h.T[a] = act ? t[a] : 1;
+        h.tpb[a] = h.bsz[a] / h.T[a];
+        h.ebs[a] = act ? h.T[a] + (h.order == 1 ? 2 : h.order == 2 ? 3 : 4) : 1;
+        h.js[a] = act ? h.T[a] + (h.order == 1 ? 3 : 5) : 1;
+    }
+    if (h.order == 2) h.ebs[0] += 1;
+    h.tiles_per_box = h.tpb[0] * h.tpb[1] * h.tpb[2];
+    h.ntiles = h.nboxes * h.tiles_per_box;
+}
+
+// a tile size is valid when it is even, at least 4 (2D and 3D alike) and
+// divides every active box extent
+bool tile_ok(const SimDev& h, int t) {
+    if (t < 4 || t % 2 != 0) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(h.dim == 2 && a == 1) && h.bsz[a] % t != 0) return false;
+    return true;
+}
+
+// TMA descriptors of the six padded E/B arrays, box = the staged tile
+pic_status encode_tmaps(pic_sim* s) {
+    EncodeTiledFn enc = get_encode_fn();
+    if (!enc) return fail(s, PIC_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    SimDev& h = s->h;
+    for (int c = 0; c < 6; ++c) {
+        cuuint64_t dims[3] = {(cuuint64_t)h.pn[0], (cuuint64_t)h.pn[1], (cuuint64_t)h.pn[2]};
+        cuuint64_t strides[2] = {(cuuint64_t)h.pn[0] * 8, (cuuint64_t)h.pn[0] * h.pn[1] * 8};
+        cuuint32_t box[3] = {(cuuint32_t)h.ebs[0], (cuuint32_t)h.ebs[1], (cuuint32_t)h.ebs[2]};
+        cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&h.tmap[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, h.F[c], dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(s, PIC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return PIC_OK;
 }
 
 // ---------------------------------------------------------------- plans ---
@@ -457,7 +502,7 @@ pic_status enqueue_step(pic_sim* s, bool with_events) {
     if (with_events) CU(s, cudaEventRecord(s->ev[0], s->stream));
     CU(s, cudaMemsetAsync(h.F[6], 0, jbytes, s->stream));
     if (h.nsp > 0) {
-        LaunchCfg cfg{s->threads, s->ctas, s->minb, s->prec};
+        LaunchCfg cfg{s->threads, s->ctas, s->minb, s->prec, s->ppt};
         CU(s, pic_launch_particles(h.dim, h.order, cfg, s->smem, s->ds, s->d, s->stream));
     }
     if (with_events) CU(s, cudaEventRecord(s->ev[1], s->stream));
@@ -503,10 +548,62 @@ pic_status configure_launch(pic_sim* s) {
     // persistent grid: every CTA resident (registers, shared memory, threads)
     // ctas_per_sm >= 2 selects the kernel variant compiled for 2 resident CTAs
     s->minb = s->ctas_per_sm >= 2 ? 2 : 1;
-    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->minb, s->threads, s->smem, s->prec);
+    int resident = pic_particle_occupancy(s->h.dim, s->h.order, s->minb, s->ppt, s->threads, s->smem, s->prec);
     if (resident < 1) return fail(s, PIC_EUNSUPPORTED, "particle kernel does not fit on an SM");
     int per_sm = std::max(1, std::min(s->ctas_per_sm, resident));
     s->ctas = s->nsm * per_sm;
+    s->graph_dirty = true;
+    return PIC_OK;
+}
+
+// Re-tiles the simulation with tile edge t in every active direction: tile
+// maps for the new staged tile, sort arrays for the new tile count, and every
+// species re-sorted by the new tiles.  Units (box chunks) are unaffected.
+pic_status retile(pic_sim* s, int t) {
+    SimDev& h = s->h;
+    if (!tile_ok(h, t)) return fail(s, PIC_EINVAL, "tile %d must be even, at least 4 and divide every box extent", t);
+    bool same = true;
+    for (int a = 0; a < 3; ++a)
+        if (!(h.dim == 2 && a == 1) && h.T[a] != t) same = false;
+    if (same) return PIC_OK;
+    {
+        SimDev probe = h;
+        const int tt[3] = {t, t, t};
+        set_tiling(probe, tt);
+        cudaDeviceProp prop;
+        CU(s, cudaGetDeviceProperties(&prop, s->device));
+        if (pic_particle_smem_bytes(h.dim, h.order, probe.T, s->threads, s->prec) > prop.sharedMemPerBlockOptin)
+            return fail(s, PIC_EUNSUPPORTED, "tile %d does not fit in shared memory", t);
+    }
+    TRY(sync_and_check(s));
+    TRY(pull_sim(s));
+    int64_t np[PIC_MAXSP] = {0, 0, 0, 0};
+    for (int i = 0; i < h.nsp; ++i)
+        CU(s, cudaMemcpyAsync(&np[i], h.sp[i].off + h.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream));
+    CU(s, cudaStreamSynchronize(s->stream));
+    const int tt[3] = {t, t, t};
+    set_tiling(h, tt);
+    TRY(encode_tmaps(s));
+    for (int i = 0; i < h.nsp; ++i) {
+        SpeciesDev& sp = h.sp[i];
+        if (h.ntiles > s->tiles_cap[i]) {
+            TRY(dalloc(s, &sp.count, h.ntiles + 1));
+            TRY(dalloc(s, &sp.cursor, h.ntiles + 1));
+            TRY(dalloc(s, &sp.off, h.ntiles + 2));
+            s->tiles_cap[i] = h.ntiles;
+        }
+        CU(s, cudaMemsetAsync(sp.count, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
+        CU(s, cudaMemsetAsync(sp.cursor, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
+        CU(s, cudaMemsetAsync(sp.off, 0, (h.ntiles + 2) * sizeof(int64_t), s->stream));
+        CU(s, cudaMemcpyAsync(sp.off + h.ntiles, &np[i], sizeof(int64_t), cudaMemcpyHostToDevice, s->stream));
+    }
+    TRY(upload_sim(s));
+    for (int i = 0; i < h.nsp; ++i) {
+        CU(s, pic_launch_initial_keys(s->d, h, i, np[i], s->stream));
+        CU(s, pic_launch_sort(s->d, h, i, s->stream));
+    }
+    TRY(sync_and_check(s));
+    TRY(pull_sim(s));
     s->graph_dirty = true;
     return PIC_OK;
 }
@@ -641,6 +738,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
     h.absorb = g.absorb_cells;
     h.capture = PIC_CAPTURE_CLOCK | PIC_CAPTURE_TIME;
     const int tdef = (g.dim == 3) ? 8 : 16;
+    int tdefs[3];
     double inv2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         bool act = !(g.dim == 2 && a == 1);
@@ -654,31 +752,27 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         h.pn[a] = h.n[a] + 2 * h.g[a];
         h.bsz[a] = g.box[a];
         h.nb[a] = h.n[a] / h.bsz[a];
+        tdefs[a] = 1;
         if (act) {
-            h.T[a] = largest_even_divisor_le(h.bsz[a], tdef);
-            if (h.T[a] == 0) {
+            // default tile edge: the largest even divisor of the box extent up
+            // to 8 (3D) or 16 (2D)
+            tdefs[a] = largest_even_divisor_le(h.bsz[a], tdef);
+            if (tdefs[a] == 0) {
                 pic_destroy(s);
                 return fail(nullptr, PIC_EUNSUPPORTED, "box extent %d has no even tile size", h.bsz[a]);
             }
             inv2 += 1.0 / (g.dx[a] * g.dx[a]);
-        } else {
-            h.T[a] = 1;
         }
-        h.tpb[a] = h.bsz[a] / h.T[a];
         h.d[a] = act ? g.dx[a] : 1.0;
         h.invd[a] = act ? 1.0 / g.dx[a] : 0.0;
     }
-    h.tiles_per_box = h.tpb[0] * h.tpb[1] * h.tpb[2];
     h.nboxes = h.nb[0] * h.nb[1] * h.nb[2];
-    h.ntiles = h.nboxes * h.tiles_per_box;
+    set_tiling(h, tdefs);
     h.dt = g.dt > 0.0 ? g.dt : (g.cfl > 0.0 ? g.cfl : 0.99) / std::sqrt(inv2);
     for (int a = 0; a < 3; ++a) {
         bool act = !(g.dim == 2 && a == 1);
         h.dtd[a] = act ? h.dt / h.d[a] : 0.0;
-        h.ebs[a] = act ? h.T[a] + (h.order == 1 ? 2 : h.order == 2 ? 3 : 4) : 1;
-        h.js[a] = act ? h.T[a] + (h.order == 1 ? 3 : 5) : 1;
     }
-    if (h.order == 2) h.ebs[0] += 1;
     h.jlo = h.order == 1 ? 1 : 2;
     if (g.dim == 3) {
         h.jfac[0] = -1.0 / (h.d[1] * h.d[2] * h.dt);
@@ -721,23 +815,10 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         return fail(nullptr, PIC_ECUDA, "schedule upload failed");
     }
     // TMA descriptors of the six padded E/B arrays
-    EncodeTiledFn enc = get_encode_fn();
-    if (!enc) {
+    if (encode_tmaps(s) != PIC_OK) {
+        g_last_error = s->err;
         pic_destroy(s);
-        return fail(nullptr, PIC_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
-    }
-    for (int c = 0; c < 6; ++c) {
-        cuuint64_t dims[3] = {(cuuint64_t)h.pn[0], (cuuint64_t)h.pn[1], (cuuint64_t)h.pn[2]};
-        cuuint64_t strides[2] = {(cuuint64_t)h.pn[0] * 8, (cuuint64_t)h.pn[0] * h.pn[1] * 8};
-        cuuint32_t box[3] = {(cuuint32_t)h.ebs[0], (cuuint32_t)h.ebs[1], (cuuint32_t)h.ebs[2]};
-        cuuint32_t es[3] = {1, 1, 1};
-        CUresult r = enc(&h.tmap[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, h.F[c], dims, strides, box,
-                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            pic_destroy(s);
-            return fail(nullptr, PIC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        }
+        return PIC_EUNSUPPORTED;
     }
     s->box_ijk.resize(3 * (size_t)h.nboxes);
     for (int64_t b = 0; b < h.nboxes; ++b) box_coords(s, b, &s->box_ijk[3 * b]);
@@ -789,6 +870,7 @@ pic_status pic_add_species(pic_sim* s, double charge, double mass, int64_t np,
     TRY(dalloc(s, &sp.count, h.ntiles + 1));
     TRY(dalloc(s, &sp.cursor, h.ntiles + 1));
     TRY(dalloc(s, &sp.off, h.ntiles + 2));
+    s->tiles_cap[idx] = h.ntiles;
     TRY(dalloc(s, &sp.np_prev, 1));
     CU(s, cudaMemsetAsync(sp.count, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
     CU(s, cudaMemsetAsync(sp.cursor, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
@@ -1165,10 +1247,16 @@ pic_status pic_set_launch(pic_sim* s, const pic_launch_cfg* cfg) {
     const int old_split = s->split;
     if (cfg->split > 0) s->split = cfg->split;
     if (cfg->precision < 0 || cfg->precision > 3) return fail(s, PIC_EINVAL, "precision must be 0, 1, 2 or 3");
+    if (cfg->ppt < 0 || cfg->ppt > 2) return fail(s, PIC_EINVAL, "ppt must be 1 or 2");
     if (cfg->precision > 0) {
         s->prec = cfg->precision - 1;
         s->graph_dirty = true;
     }
+    if (cfg->ppt > 0) {
+        s->ppt = cfg->ppt;
+        s->graph_dirty = true;
+    }
+    if (cfg->tile > 0) TRY(retile(s, cfg->tile));
     const int old = s->ctas;
     TRY(configure_launch(s));
     if (s->ctas != old || s->split != old_split) TRY(replan(s));
@@ -1181,6 +1269,8 @@ pic_status pic_get_launch(const pic_sim* s, pic_launch_cfg* cfg) {
     cfg->ctas_per_sm = s->ctas / std::max(1, s->nsm);
     cfg->split = s->split;
     cfg->precision = s->prec + 1;
+    cfg->tile = s->h.T[0];
+    cfg->ppt = s->ppt;
     return PIC_OK;
 }
 
@@ -1188,13 +1278,6 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     TRY(check(s));
     if (steps_per_candidate < 1) return fail(s, PIC_EINVAL, "steps_per_candidate must be >= 1");
     TRY(ensure_ready(s));
-    // candidates: threads per CTA x resident CTAs per SM (register budget of the
-    // kernel variant) x work units per worker (how finely heavy boxes are cut)
-    const int threads_c[2] = {128, 256};
-    const int cps_c[2] = {1, 2};
-    const int split_c[3] = {4, 16, 64};
-    float best_ms = 1e30f;
-    pic_launch_cfg best_cfg{s->threads, s->ctas_per_sm, s->split, 0};
     // the events and the profiling switch are restored on every way out
     struct Guard {
         pic_sim* s;
@@ -1208,31 +1291,79 @@ pic_status pic_autotune(pic_sim* s, int steps_per_candidate, pic_launch_cfg* bes
     } g{s, s->profiling};
     CU(s, cudaEventCreate(&g.a));
     CU(s, cudaEventCreate(&g.b));
-    cudaEvent_t a = g.a, b = g.b;
     s->profiling = false;
-    const bool splits = s->lb_set && s->lb.mode != PIC_LB_NONE;
-    for (int t : threads_c)
-        for (int c : cps_c)
-            for (int sp : split_c) {
-                if (!splits && sp != split_c[1]) continue;  // no cut boxes without balancing
-                pic_launch_cfg cfg{t, c, sp, 0};
-                TRY(pic_set_launch(s, &cfg));
-                if (s->ctas / s->nsm != c) continue;  // not resident: skip
-                TRY(pic_step(s, 1));
-                CU(s, cudaEventRecord(a, s->stream));
-                TRY(pic_step(s, steps_per_candidate));
-                CU(s, cudaEventRecord(b, s->stream));
-                CU(s, cudaEventSynchronize(b));
-                float ms = 0;
-                cudaEventElapsedTime(&ms, a, b);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_cfg = pic_launch_cfg{t, c, sp, 0};
-                }
-            }
+    pic_launch_cfg cur{};
+    TRY(pic_get_launch(s, &cur));
+    cur.precision = 0;
+    float best_ms = 1e30f;
+    pic_launch_cfg best_cfg = cur;
+    // times one candidate on real steps; *ms = 1e30 when it is not resident
+    auto trial = [&](const pic_launch_cfg& c, float* ms) -> pic_status {
+        *ms = 1e30f;
+        TRY(pic_set_launch(s, &c));
+        if (s->ctas / s->nsm != c.ctas_per_sm) return PIC_OK;  // not resident: skip
+        TRY(pic_step(s, 1));
+        CU(s, cudaEventRecord(g.a, s->stream));
+        TRY(pic_step(s, steps_per_candidate));
+        CU(s, cudaEventRecord(g.b, s->stream));
+        CU(s, cudaEventSynchronize(g.b));
+        cudaEventElapsedTime(ms, g.a, g.b);
+        return PIC_OK;
+    };
+    auto consider = [&](const pic_launch_cfg& c) -> pic_status {
+        float ms;
+        TRY(trial(c, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_cfg = c;
+        }
+        return PIC_OK;
+    };
+    // stage 1: tile size x particles per thread
+    const int tmax = s->h.dim == 3 ? 8 : 32;
+    for (int t = 4; t <= tmax; t += 2) {
+        if (!tile_ok(s->h, t)) continue;
+        SimDev probe = s->h;
+        const int tt[3] = {t, t, t};
+        set_tiling(probe, tt);
+        cudaDeviceProp prop;
+        CU(s, cudaGetDeviceProperties(&prop, s->device));
+        if (pic_particle_smem_bytes(probe.dim, probe.order, probe.T, 256, s->prec) > prop.sharedMemPerBlockOptin)
+            continue;
+        for (int ppt = 1; ppt <= 2; ++ppt) {
+            pic_launch_cfg c = best_ms < 1e29f ? best_cfg : cur;
+            c.tile = t;
+            c.ppt = ppt;
+            TRY(consider(c));
+        }
+    }
+    // stage 2: threads per CTA x resident CTAs per SM (register budget of the kernel variant)
+    const pic_launch_cfg after1 = best_cfg;
+    for (int threads : {128, 256})
+        for (int cps : {1, 2}) {
+            if (threads == after1.threads && cps == after1.ctas_per_sm) continue;
+            pic_launch_cfg c = after1;
+            c.threads = threads;
+            c.ctas_per_sm = cps;
+            TRY(consider(c));
+        }
+    // stage 3: work units per worker (how finely heavy boxes are cut), only
+    // when load balancing cuts boxes
+    if (s->lb_set && s->lb.mode != PIC_LB_NONE) {
+        const pic_launch_cfg after2 = best_cfg;
+        for (int sp : {4, 16, 64}) {
+            if (sp == after2.split) continue;
+            pic_launch_cfg c = after2;
+            c.split = sp;
+            TRY(consider(c));
+        }
+    }
     s->profiling = g.prof;
     TRY(pic_set_launch(s, &best_cfg));
-    if (best) *best = best_cfg;
+    if (best) {
+        *best = best_cfg;
+        best->precision = s->prec + 1;
+    }
     return sync_and_check(s);
 }
 

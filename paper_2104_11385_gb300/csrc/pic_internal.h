@@ -116,27 +116,28 @@ int pic_sm_count();
 struct LaunchCfg {
     int threads;
     int ctas;
-    int minb;  // register budget variant of the particle kernel: 1 or 2 CTAs per SM
-    int prec;  // arithmetic of the particle push: 0 FP64, 1 float-float
+    int minb;     // register budget variant of the particle kernel: 1 or 2 CTAs per SM
+    int prec;     // arithmetic of the particle push: 0 FP64, 1 float-float, 2 FP32
+    int ppt = 1;  // particles per thread per loop iteration (1 or 2)
 };
 // dynamic shared memory of the particle kernel; prec 0 FP64, 1 float-float, 2 FP32
 size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, int prec);
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem);  // outside graph capture
-int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem,
+int pic_particle_occupancy(int dim, int order, int minb, int ppt, int threads, size_t smem,
                            int prec);  // resident CTAs per SM
-// per-precision instantiations (pic_particles_f64.cu, pic_particles_dd.cu)
-cudaError_t pic_launch_particles_p0(int dim, int order, const LaunchCfg& cfg, size_t smem,
-                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
-cudaError_t pic_launch_particles_p1(int dim, int order, const LaunchCfg& cfg, size_t smem,
-                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
-cudaError_t pic_prepare_particles_p0(int dim, int order, size_t smem);
-cudaError_t pic_prepare_particles_p1(int dim, int order, size_t smem);
-int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t smem);
-int pic_particle_occupancy_p1(int dim, int order, int minb, int threads, size_t smem);
-cudaError_t pic_launch_particles_p2(int dim, int order, const LaunchCfg& cfg, size_t smem,
-                                    const SchedDev* sched, SimDev* sims, cudaStream_t st);
-cudaError_t pic_prepare_particles_p2(int dim, int order, size_t smem);
-int pic_particle_occupancy_p2(int dim, int order, int minb, int threads, size_t smem);
+// per-precision, per-dimensionality instantiations (pic_particles_<prec>_<dim>d.cu);
+// the dispatchers below (pic_particles.cu) pick one by precision and dim
+#define PIC_DECLARE_PARTICLE_TU(SUF)                                                                     \
+    cudaError_t pic_launch_particles_##SUF(int order, const LaunchCfg& cfg, size_t smem,                 \
+                                           const SchedDev* sched, SimDev* sims, cudaStream_t st);        \
+    cudaError_t pic_prepare_particles_##SUF(int order, size_t smem);                                      \
+    int pic_particle_occupancy_##SUF(int order, int minb, int ppt, int threads, size_t smem);
+PIC_DECLARE_PARTICLE_TU(p0_d3)
+PIC_DECLARE_PARTICLE_TU(p0_d2)
+PIC_DECLARE_PARTICLE_TU(p1_d3)
+PIC_DECLARE_PARTICLE_TU(p1_d2)
+PIC_DECLARE_PARTICLE_TU(p2_d3)
+PIC_DECLARE_PARTICLE_TU(p2_d2)
 // self-test of the device's bounded wait: one CTA waits on an mbarrier that
 // nothing arrives at; after limit_ns it sets PIC_DERR_WAIT_TIMEOUT in *err
 cudaError_t pic_launch_selftest_wait(int32_t* err, uint64_t limit_ns, cudaStream_t st);

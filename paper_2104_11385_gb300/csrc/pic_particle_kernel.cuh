@@ -1,7 +1,7 @@
 // pic_particle_kernel.cuh -- the particle side of the PIC cycle on sm_103a,
 // templated on the arithmetic of the particle push (included by one
-// translation unit per precision: pic_particles_f64.cu, pic_particles_dd.cu,
-// pic_particles_f32.cu).
+// translation unit per precision and dimensionality:
+// pic_particles_{f64,dd,f32}_{3d,2d}.cu).
 //
 // pic_particle_kernel: persistent CTAs pull work units (a chunk of one box's
 // particles) from cost-ordered lists.  For every tile (sub-box) a unit touches,
@@ -784,6 +784,26 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<
     }
 }
 
+// One particle's stored state as read from HBM (positions in global cell
+// units, momenta and weight as stored); loaded ahead of its push so that the
+// loads of several particles per thread can be in flight together.
+struct PIn {
+    double X, Y, Z, u0, u1, u2, w;
+};
+
+template <int DIM>
+__device__ __forceinline__ PIn load_one(const SpeciesDev& sp, int64_t p) {
+    PIn in;
+    in.X = sp.cur[0][p];
+    in.Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
+    in.Z = sp.cur[2][p];
+    in.u0 = sp.cur[3][p];
+    in.u1 = sp.cur[4][p];
+    in.u2 = sp.cur[5][p];
+    in.w = sp.cur[6][p];
+    return in;
+}
+
 // Gather, Boris push, and deposit of one particle.  Particles that keep their
 // support in every direction deposit at once on the small window; the others
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
@@ -791,12 +811,13 @@ template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
                                          const R* __restrict__ sEB, const JView<typename JAcc<R>::type>& V,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
-                                         const R* jf, const R* dtd, R kq, R qs, int64_t p, int32_t* err) {
+                                         const R* jf, const R* dtd, R kq, R qs, int64_t p, const PIn& in,
+                                         int32_t* err) {
     using A = Arith<R>;
-    double X = sp.cur[0][p], Z = sp.cur[2][p];
-    double Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
-    const R u0 = A::from(sp.cur[3][p]), u1 = A::from(sp.cur[4][p]), u2 = A::from(sp.cur[5][p]);
-    const R qw = qs * A::from(sp.cur[6][p]);
+    double X = in.X, Z = in.Z;
+    double Y = (DIM == 3) ? in.Y : 0.0;
+    const R u0 = A::from(in.u0), u1 = A::from(in.u1), u2 = A::from(in.u2);
+    const R qw = qs * A::from(in.w);
 
     // ---- gather at x^n: node and half-node supports per direction (tile-local nodes)
     Support<ORDER, R> nd[3], hf[3];
@@ -1015,7 +1036,9 @@ struct SimConsts {
 // positions and index math stay FP64 in all three; the current goes to the
 // global FP64 J by L2 reductions, except in the FP32 variant, whose shared
 // tile sums in FP32).
-template <int DIM, int ORDER, int MINB, int PREC>
+// PPT = particles per thread per loop iteration: their HBM loads are issued
+// together before the first of them is pushed.
+template <int DIM, int ORDER, int MINB, int PREC, int PPT>
 __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                               SimDev* __restrict__ sims) {
     using R = typename std::conditional<PREC == 1, dd, typename std::conditional<PREC == 2, float, double>::type>::type;
@@ -1189,18 +1212,27 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     const JView<JT> V = j_view<JT>(S, cur, sJ, P);
                     double* sQw = sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
                     volatile unsigned* vtail = s_qtail + warp;
-                    for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += blockDim.x) {
-                        const int64_t p = p0 + lane;
-                        if (p < s1)
-                            push_one<R, DIM, ORDER>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq, qs,
-                                                    p, sd->err);
-                        __syncwarp();
-                        const unsigned head = s_qhead[warp], tail = *vtail;
-                        if (tail - head >= 32u) {
-                            drain<R, DIM, ORDER>(S, cur, V, sQw, head, 32u, K.jf, sd->err);
+                    for (int64_t p0 = s0 + warp * (32 * PPT); p0 < s1; p0 += (int64_t)blockDim.x * PPT) {
+                        PIn in[PPT];
+#pragma unroll
+                        for (int q = 0; q < PPT; ++q) {
+                            const int64_t p = p0 + q * 32 + lane;
+                            if (p < s1) in[q] = load_one<DIM>(sp, p);
+                        }
+#pragma unroll
+                        for (int q = 0; q < PPT; ++q) {
+                            const int64_t p = p0 + q * 32 + lane;
+                            if (p < s1)
+                                push_one<R, DIM, ORDER>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq,
+                                                        qs, p, in[q], sd->err);
                             __syncwarp();
-                            if (lane == 0) s_qhead[warp] = head + 32u;
-                            __syncwarp();
+                            const unsigned head = s_qhead[warp], tail = *vtail;
+                            if (tail - head >= 32u) {
+                                drain<R, DIM, ORDER>(S, cur, V, sQw, head, 32u, K.jf, sd->err);
+                                __syncwarp();
+                                if (lane == 0) s_qhead[warp] = head + 32u;
+                                __syncwarp();
+                            }
                         }
                     }
                     __syncwarp();
@@ -1249,41 +1281,71 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
 template <int DIM, int ORDER, int PREC>
 static cudaError_t launch_particles_t(const LaunchCfg& cfg, size_t smem, const SchedDev* sched,
                                       SimDev* sims, cudaStream_t st) {
-    if (cfg.minb == 2)
-        pic_particle_kernel<DIM, ORDER, 2, PREC><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
-    else
-        pic_particle_kernel<DIM, ORDER, 1, PREC><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    const bool two = cfg.ppt == 2;
+    if (cfg.minb == 2) {
+        if (two) pic_particle_kernel<DIM, ORDER, 2, PREC, 2><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+        else pic_particle_kernel<DIM, ORDER, 2, PREC, 1><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    } else {
+        if (two) pic_particle_kernel<DIM, ORDER, 1, PREC, 2><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+        else pic_particle_kernel<DIM, ORDER, 1, PREC, 1><<<cfg.ctas, cfg.threads, smem, st>>>(sched, sims);
+    }
     return cudaGetLastError();
+}
+
+template <class K>
+static cudaError_t set_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <int DIM, int ORDER, int PREC>
 static cudaError_t prepare_t(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 1, PREC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pic_particle_kernel<DIM, ORDER, 2, PREC>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem(pic_particle_kernel<DIM, ORDER, 1, PREC, 1>, smem);
+    if (e == cudaSuccess) e = set_smem(pic_particle_kernel<DIM, ORDER, 2, PREC, 1>, smem);
+    if (e == cudaSuccess) e = set_smem(pic_particle_kernel<DIM, ORDER, 1, PREC, 2>, smem);
+    if (e == cudaSuccess) e = set_smem(pic_particle_kernel<DIM, ORDER, 2, PREC, 2>, smem);
+    return e;
 }
 
 template <int DIM, int ORDER, int PREC>
-static int occupancy_t(int minb, int threads, size_t smem) {
+static int occupancy_t(int minb, int ppt, int threads, size_t smem) {
     int n = 0;
-    cudaError_t e = minb == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &n, pic_particle_kernel<DIM, ORDER, 2, PREC>, threads, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &n, pic_particle_kernel<DIM, ORDER, 1, PREC>, threads, smem);
+    cudaError_t e;
+    if (minb == 2)
+        e = ppt == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<DIM, ORDER, 2, PREC, 2>,
+                                                                     threads, smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<DIM, ORDER, 2, PREC, 1>,
+                                                                     threads, smem);
+    else
+        e = ppt == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<DIM, ORDER, 1, PREC, 2>,
+                                                                     threads, smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pic_particle_kernel<DIM, ORDER, 1, PREC, 1>,
+                                                                     threads, smem);
     return e == cudaSuccess ? n : 0;
 }
 
-// dispatch over (dim, order) for one precision
-#define PIC_DISPATCH_DO(FN, ...)                                         \
-    do {                                                                 \
-        if (dim == 3 && order == 1) return FN<3, 1, PIC_PREC>(__VA_ARGS__); \
-        if (dim == 3 && order == 2) return FN<3, 2, PIC_PREC>(__VA_ARGS__); \
-        if (dim == 3 && order == 3) return FN<3, 3, PIC_PREC>(__VA_ARGS__); \
-        if (dim == 2 && order == 1) return FN<2, 1, PIC_PREC>(__VA_ARGS__); \
-        if (dim == 2 && order == 2) return FN<2, 2, PIC_PREC>(__VA_ARGS__); \
-        if (dim == 2 && order == 3) return FN<2, 3, PIC_PREC>(__VA_ARGS__); \
+// dispatch over the shape order for one precision (PIC_PREC) and one
+// dimensionality (PIC_DIM): each translation unit instantiates one pair
+#define PIC_DISPATCH_DO(FN, ...)                                            \
+    do {                                                                    \
+        if (order == 1) return FN<PIC_DIM, 1, PIC_PREC>(__VA_ARGS__);       \
+        if (order == 2) return FN<PIC_DIM, 2, PIC_PREC>(__VA_ARGS__);       \
+        if (order == 3) return FN<PIC_DIM, 3, PIC_PREC>(__VA_ARGS__);       \
     } while (0)
 
 }  // namespace
+
+// the three entry points of one translation unit, suffix SUF = p<prec>_d<dim>
+#define PIC_DEFINE_PARTICLE_TU(SUF)                                                                      \
+    cudaError_t pic_launch_particles_##SUF(int order, const LaunchCfg& cfg, size_t smem,                 \
+                                           const SchedDev* sched, SimDev* sims, cudaStream_t st) {       \
+        PIC_DISPATCH_DO(launch_particles_t, cfg, smem, sched, sims, st);                                  \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    cudaError_t pic_prepare_particles_##SUF(int order, size_t smem) {                                     \
+        PIC_DISPATCH_DO(prepare_t, smem);                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    int pic_particle_occupancy_##SUF(int order, int minb, int ppt, int threads, size_t smem) {            \
+        PIC_DISPATCH_DO(occupancy_t, minb, ppt, threads, smem);                                           \
+        return 0;                                                                                         \
+    }

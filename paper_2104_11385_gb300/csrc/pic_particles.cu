@@ -188,24 +188,42 @@ int pic_sm_count() {
     return n;
 }
 
-// particle kernel: dispatch on the arithmetic of the push
+// particle kernel: dispatch on the arithmetic of the push and the dimensionality
 cudaError_t pic_launch_particles(int dim, int order, const LaunchCfg& cfg, size_t smem,
                                  const SchedDev* sched, SimDev* sims, cudaStream_t st) {
-    if (cfg.prec == 2) return pic_launch_particles_p2(dim, order, cfg, smem, sched, sims, st);
-    return cfg.prec == 1 ? pic_launch_particles_p1(dim, order, cfg, smem, sched, sims, st)
-                         : pic_launch_particles_p0(dim, order, cfg, smem, sched, sims, st);
+    if (cfg.prec == 2)
+        return dim == 3 ? pic_launch_particles_p2_d3(order, cfg, smem, sched, sims, st)
+                        : pic_launch_particles_p2_d2(order, cfg, smem, sched, sims, st);
+    if (cfg.prec == 1)
+        return dim == 3 ? pic_launch_particles_p1_d3(order, cfg, smem, sched, sims, st)
+                        : pic_launch_particles_p1_d2(order, cfg, smem, sched, sims, st);
+    return dim == 3 ? pic_launch_particles_p0_d3(order, cfg, smem, sched, sims, st)
+                    : pic_launch_particles_p0_d2(order, cfg, smem, sched, sims, st);
 }
 
 cudaError_t pic_prepare_particles(int dim, int order, size_t smem) {
-    cudaError_t e = pic_prepare_particles_p0(dim, order, smem);
-    if (e == cudaSuccess) e = pic_prepare_particles_p1(dim, order, smem);
-    return e != cudaSuccess ? e : pic_prepare_particles_p2(dim, order, smem);
+    cudaError_t e;
+    if (dim == 3) {
+        e = pic_prepare_particles_p0_d3(order, smem);
+        if (e == cudaSuccess) e = pic_prepare_particles_p1_d3(order, smem);
+        if (e == cudaSuccess) e = pic_prepare_particles_p2_d3(order, smem);
+    } else {
+        e = pic_prepare_particles_p0_d2(order, smem);
+        if (e == cudaSuccess) e = pic_prepare_particles_p1_d2(order, smem);
+        if (e == cudaSuccess) e = pic_prepare_particles_p2_d2(order, smem);
+    }
+    return e;
 }
 
-int pic_particle_occupancy(int dim, int order, int minb, int threads, size_t smem, int prec) {
-    if (prec == 2) return pic_particle_occupancy_p2(dim, order, minb, threads, smem);
-    return prec == 1 ? pic_particle_occupancy_p1(dim, order, minb, threads, smem)
-                     : pic_particle_occupancy_p0(dim, order, minb, threads, smem);
+int pic_particle_occupancy(int dim, int order, int minb, int ppt, int threads, size_t smem, int prec) {
+    if (prec == 2)
+        return dim == 3 ? pic_particle_occupancy_p2_d3(order, minb, ppt, threads, smem)
+                        : pic_particle_occupancy_p2_d2(order, minb, ppt, threads, smem);
+    if (prec == 1)
+        return dim == 3 ? pic_particle_occupancy_p1_d3(order, minb, ppt, threads, smem)
+                        : pic_particle_occupancy_p1_d2(order, minb, ppt, threads, smem);
+    return dim == 3 ? pic_particle_occupancy_p0_d3(order, minb, ppt, threads, smem)
+                    : pic_particle_occupancy_p0_d2(order, minb, ppt, threads, smem);
 }
 
 static int grid_for(int64_t n, int threads) {

@@ -1,0 +1,6 @@
+// pic_particles_dd_2d.cu -- float-float instantiation of the particle kernel (the mixed-precision variant), 2D shapes of order 1-3.
+#define PIC_PREC 1
+#define PIC_DIM 2
+#include "pic_particle_kernel.cuh"
+
+PIC_DEFINE_PARTICLE_TU(p1_d2)

@@ -1,23 +1,9 @@
-// pic_particles_f64.cu -- FP64 instantiation of the particle kernel, and the
-// shared-memory size of its tiles.
+// pic_particles_f64_3d.cu -- FP64 instantiation of the particle kernel, 3D shapes of order 1-3.
 #define PIC_PREC 0
+#define PIC_DIM 3
 #include "pic_particle_kernel.cuh"
 
-cudaError_t pic_launch_particles_p0(int dim, int order, const LaunchCfg& cfg, size_t smem,
-                                        const SchedDev* sched, SimDev* sims, cudaStream_t st) {
-    PIC_DISPATCH_DO(launch_particles_t, cfg, smem, sched, sims, st);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t pic_prepare_particles_p0(int dim, int order, size_t smem) {
-    PIC_DISPATCH_DO(prepare_t, smem);
-    return cudaErrorInvalidValue;
-}
-
-int pic_particle_occupancy_p0(int dim, int order, int minb, int threads, size_t smem) {
-    PIC_DISPATCH_DO(occupancy_t, minb, threads, smem);
-    return 0;
-}
+PIC_DEFINE_PARTICLE_TU(p0_d3)
 
 size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, int prec) {
     int ebs[3], js[3];

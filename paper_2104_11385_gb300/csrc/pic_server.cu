@@ -267,7 +267,7 @@ pic_status rebuild_units(pic_server* s) {
     SCU(s, cudaStreamSynchronize(s->stream));
     if (!s->active_slots.empty()) {
         SCU(s, pic_prepare_particles(s->desc.dim, s->desc.shape_order, s->smem));
-        int per_sm = pic_particle_occupancy(s->desc.dim, s->desc.shape_order, 1, s->threads, s->smem, 0);
+        int per_sm = pic_particle_occupancy(s->desc.dim, s->desc.shape_order, 1, 1, s->threads, s->smem, 0);
         s->ctas = s->nsm * std::max(1, std::min(per_sm, 2));
     }
     s->dirty = false;

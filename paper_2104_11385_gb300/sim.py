@@ -211,19 +211,20 @@ class Simulation:
         out["id"] = ids
         return out
 
-    def set_launch(self, threads=0, ctas_per_sm=0, split=0, precision=0):
-        c = L.LaunchCfg(int(threads), int(ctas_per_sm), int(split), int(precision))
+    def set_launch(self, threads=0, ctas_per_sm=0, split=0, precision=0, tile=0, ppt=0):
+        c = L.LaunchCfg(int(threads), int(ctas_per_sm), int(split), int(precision), int(tile), int(ppt))
         self._check(self._lib.pic_set_launch(self._h, ctypes.byref(c)))
 
     def get_launch(self):
         c = L.LaunchCfg()
         self._check(self._lib.pic_get_launch(self._h, ctypes.byref(c)))
-        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split, "precision": c.precision}
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split, "precision": c.precision,
+                "tile": c.tile, "ppt": c.ppt}
 
     def autotune(self, steps_per_candidate=2):
         c = L.LaunchCfg()
         self._check(self._lib.pic_autotune(self._h, int(steps_per_candidate), ctypes.byref(c)))
-        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split}
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split, "tile": c.tile, "ppt": c.ppt}
 
     def set_profiling(self, on=True):
         self._check(self._lib.pic_set_profiling(self._h, 1 if on else 0))

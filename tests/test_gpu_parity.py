@@ -214,6 +214,67 @@ def test_schedule_does_not_change_physics(sched, policy, cost):
     compare(sim, ref, wl)
 
 
+TILE_CASES = [
+    # dim, ncell, box, order, tile, ppt
+    (3, (16, 16, 16), (8, 8, 8), 1, 4, 2),
+    (3, (16, 16, 24), (8, 8, 8), 2, 4, 1),
+    (3, (16, 16, 16), (8, 8, 8), 3, 4, 2),
+    (2, (64, 1, 64), (32, 1, 32), 1, 32, 2),
+    (2, (64, 1, 64), (32, 1, 32), 3, 8, 1),
+    (3, (16, 16, 16), (8, 8, 8), 1, 8, 2),
+]
+
+
+@pytest.mark.parametrize("case", TILE_CASES, ids=[f"{c[0]}d_o{c[3]}_t{c[4]}_ppt{c[5]}" for c in TILE_CASES])
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp64", "float_float"])
+def test_tile_size_and_particles_per_thread_do_not_change_physics(case, precision):
+    """Every tile size the autotuner may pick, and two particles per thread,
+    against the oracle at 1e-10 (random relativistic plasma, many crossings)."""
+    dim, n, box, order, tile, ppt = case
+    dx = (0.3, 0.3 if dim == 3 else 1.0, 0.3)
+    wl = workloads.random_plasma(400 + tile + order, dim, n, box, dx, order, nspecies=2, npart=4000, umax=1.5)
+    fields = workloads.random_fields(8, n, amp=0.1)
+    sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
+    sim.set_launch(tile=tile, ppt=ppt, precision=precision)
+    assert sim.get_launch()["tile"] == tile and sim.get_launch()["ppt"] == ppt
+    sim.step(8)
+    ref.step(8)
+    compare(sim, ref, wl)
+
+
+def test_retile_between_steps():
+    """A tile change after some steps re-sorts every species; the run stays on
+    the oracle's trajectory, and bad tile sizes are refused."""
+    wl = workloads.random_plasma(410, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=2,
+                                 npart=4000, umax=1.0)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_lb_params(mode=pic.LB_DYNAMIC, interval=2, theta=0.0, split=8)
+    sim.step(3)
+    sim.set_launch(tile=4)
+    sim.step(3)
+    sim.set_launch(tile=8, ppt=2)
+    sim.step(3)
+    ref.step(9)
+    compare(sim, ref, wl)
+    for bad in (3, 6, 16, 2):
+        with pytest.raises(pic.PicError):
+            sim.set_launch(tile=bad)
+    assert sim.get_launch()["tile"] == 8
+
+
+def test_autotune_searches_tile_and_particles_per_thread():
+    wl = workloads.lognormal(seed=9, nbox=(4, 4, 4), box=8, median=1500.0, sigma=1.0, order=1)
+    sim = make_gpu(wl)
+    sim.set_lb_params(mode=pic.LB_DYNAMIC, interval=5, theta=0.1)
+    best = sim.autotune(steps_per_candidate=1)
+    assert best["tile"] in (4, 8) and best["ppt"] in (1, 2)
+    assert best["threads"] in (128, 256) and best["ctas_per_sm"] in (1, 2) and best["split"] in (4, 16, 64)
+    got = sim.get_launch()
+    assert all(got[k] == best[k] for k in best)
+    sim.step(2)
+    sim.sync()
+
+
 @pytest.mark.parametrize("threads,cps", [(128, 1), (256, 2)])
 def test_launch_configuration_does_not_change_physics(threads, cps):
     wl = workloads.random_plasma(78, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=1,

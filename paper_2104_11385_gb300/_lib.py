@@ -124,6 +124,18 @@ SIGNATURES = [
     ("pic_set_profiling", _int, [_vp, _int]),
     ("pic_get_stats", _int, [_vp, ctypes.POINTER(Stats)]),
     ("pic_probe_fp64_fma", _int, [_i64, _pd]),
+    ("pic_shard_halo_cells", _int, [ctypes.POINTER(GridDesc), _pi32, _int, _int, _int, _pi64, _pi64]),
+    ("pic_shard_moved_cells", _int, [ctypes.POINTER(GridDesc), _pi32, _pi32, _int, _int, _pi64, _pi64]),
+    ("pic_shard_set_owner", _int, [_vp, _pi32, _int]),
+    ("pic_shard_pack", _int, [_vp, _int, _int, _vp, _i64, _vp]),
+    ("pic_shard_unpack", _int, [_vp, _int, _int, _vp, _i64, _vp, _int]),
+    ("pic_shard_push", _int, [_vp]),
+    ("pic_shard_field_stage", _int, [_vp, _int]),
+    ("pic_shard_rekey", _int, [_vp]),
+    ("pic_shard_take_leaving", _int, [_vp, _int, _int, _pi64]),
+    ("pic_shard_read_leaving", _int, [_vp, _int, _int, ctypes.POINTER(_vp), _vp]),
+    ("pic_shard_add_arriving", _int, [_vp, _int, _i64, ctypes.POINTER(_vp), _vp]),
+    ("pic_shard_finish", _int, [_vp, _int]),
     ("pic_destroy", _int, [_vp]),
     ("pic_last_error", ctypes.c_char_p, [_vp]),
     ("pic_server_create", _int, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),

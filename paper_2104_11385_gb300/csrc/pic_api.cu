@@ -24,6 +24,7 @@
 #include "pic_balance.h"
 #include "pic_bin.h"
 #include "pic_internal.h"
+#include "pic_sim.h"
 
 namespace {
 
@@ -47,66 +48,7 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-struct Plan {
-    std::vector<UnitDev> units;      // in list order
-    std::vector<int32_t> list_off;   // nlists + 1
-    std::vector<double> unit_cost;   // model cost of each unit (list order)
-    std::vector<int32_t> unit_worker;
-    int nlists = 1;
-    int n_workers = 1;
-};
-
 }  // namespace
-
-struct pic_sim {
-    std::string err = "no error";
-    bool poisoned = false;
-    bool stepped = false;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    SimDev h{};            // host mirror (species buffer pointers are swapped on the device)
-    SimDev* d = nullptr;   // device copy
-    SchedDev hs{};
-    SchedDev* ds = nullptr;
-    int64_t units_cap = 0;
-    double rho0 = 0.0;
-    std::vector<void*> allocs;
-    int64_t bytes = 0;  // device bytes allocated by the handle
-    int64_t np_init[PIC_MAXSP] = {0, 0, 0, 0};
-    // launch configuration
-    int nsm = 0;
-    int threads = 256;
-    int ctas_per_sm = 1;
-    int split = 16;
-    int ctas = 0;
-    int minb = 1;
-    int prec = 0;  // 0 FP64, 1 float-float, 2 FP32 particle push
-    int ppt = 1;   // particles per thread per loop iteration
-    size_t smem = 0;
-    int64_t tiles_cap[PIC_MAXSP] = {0, 0, 0, 0};  // sort arrays allocated for this many tiles
-    // load balancing
-    pic_lb_params lb{};
-    bool lb_set = false;
-    bool static_done = false;
-    Plan plan;
-    std::vector<double> last_costs;
-    std::vector<int64_t> last_np;
-    int64_t step_count = 0;
-    std::vector<int32_t> box_ijk;
-    // graph
-    cudaGraphExec_t graph = nullptr;
-    bool graph_dirty = true;
-    int kernels_per_step = 0;
-    // profiling
-    bool profiling = false;
-    pic_stats stats{};
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    // device scratch
-    int64_t* d_scalar = nullptr;
-    int64_t* d_box_np = nullptr;
-    std::vector<pic_lb_result> lb_log;
-};
 
 namespace {
 
@@ -277,7 +219,7 @@ int n_workers_for(const pic_sim* s, const pic_lb_params& p) {
 // builds the plan from units and their mapping
 void build_plan(pic_sim* s, const std::vector<pic::Unit>& units, const std::vector<int32_t>& assign,
                 int n_workers, int sched, bool box_order = false) {
-    Plan& P = s->plan;
+    SimPlan& P = s->plan;
     P.units.clear();
     P.unit_cost.clear();
     P.unit_worker.clear();
@@ -313,7 +255,7 @@ void build_plan(pic_sim* s, const std::vector<pic::Unit>& units, const std::vect
 }
 
 pic_status upload_plan(pic_sim* s) {
-    Plan& P = s->plan;
+    SimPlan& P = s->plan;
     int64_t nu = (int64_t)P.units.size();
     if (nu > s->units_cap) {
         int64_t cap = std::max<int64_t>(nu, 2 * s->units_cap);
@@ -351,7 +293,7 @@ pic_status initial_plan(pic_sim* s) {
     pic::sfc(ones.data(), s->box_ijk.data(), nb, s->h.dim, nw, assign.data());
     if (sched == PIC_SCHED_QUEUE) {
         // queue: boxes in index order
-        Plan& P = s->plan;
+        SimPlan& P = s->plan;
         P.units.clear();
         P.unit_cost.assign(nb, 1.0);
         P.unit_worker = assign;
@@ -433,7 +375,7 @@ pic_status validate_lb(pic_sim* s, const pic_lb_params* p) {
 // E (Eq. 1) of the work-unit mapping in force for per-box costs; a box's
 // cost is divided evenly over its units
 double plan_efficiency(const pic_sim* s, const std::vector<double>& costs) {
-    const Plan& P = s->plan;
+    const SimPlan& P = s->plan;
     std::vector<double> uc(P.units.size());
     for (size_t i = 0; i < P.units.size(); ++i) uc[i] = costs[P.units[i].box] / (double)P.units[i].nchunks;
     return pic::lb_efficiency(uc.data(), P.unit_worker.data(), (int64_t)uc.size(), P.n_workers);
@@ -640,6 +582,39 @@ pic_status replan(pic_sim* s) {
 pic_status pic_record_error(pic_status st, const char* msg) {
     g_last_error = msg;
     return st;
+}
+
+// ---- helpers for the other host files of the library (pic_sim.h) ----
+pic_status pic_sim_fail(pic_sim* s, pic_status st, const char* msg) { return fail(s, st, "%s", msg); }
+pic_status pic_sim_check(pic_sim* s) { return check(s); }
+pic_status pic_sim_upload(pic_sim* s) { return upload_sim(s); }
+pic_status pic_sim_pull(pic_sim* s) { return pull_sim(s); }
+pic_status pic_sim_sync(pic_sim* s) { return sync_and_check(s); }
+pic_status pic_sim_dalloc(pic_sim* s, void** p, size_t bytes) {
+    char* q = nullptr;
+    pic_status st = dalloc(s, &q, bytes);
+    *p = q;
+    return st;
+}
+void pic_sim_dfree(pic_sim* s, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < s->allocs.size(); ++i)
+        if (s->allocs[i] == p) {
+            cudaFree(p);
+            s->allocs.erase(s->allocs.begin() + (long)i);
+            return;
+        }
+}
+pic_status pic_sim_ensure_ready(pic_sim* s) { return ensure_ready(s); }
+pic_status pic_sim_launch_push(pic_sim* s) {
+    const SimDev& h = s->h;
+    const int64_t jbytes = (int64_t)h.pn[0] * h.pn[1] * h.pn[2] * 3 * sizeof(double);
+    CU(s, cudaMemsetAsync(h.F[6], 0, jbytes, s->stream));
+    if (h.nsp > 0) {
+        LaunchCfg cfg{s->threads, s->ctas, s->minb, s->prec, s->ppt};
+        CU(s, pic_launch_particles(h.dim, h.order, cfg, s->smem, s->ds, s->d, s->stream));
+    }
+    return PIC_OK;
 }
 
 // ---- hooks for the request server (same library, not exported) ----
@@ -1092,7 +1067,7 @@ pic_status pic_rebalance(pic_sim* s, const pic_lb_params* params, pic_lb_result*
     TRY(rebalance(s, p, p.theta, out));
     if (assign_out) {
         for (int64_t b = 0; b < s->h.nboxes; ++b) assign_out[b] = -1;
-        const Plan& P = s->plan;
+        const SimPlan& P = s->plan;
         for (size_t i = 0; i < P.units.size(); ++i)
             if (P.units[i].chunk == 0) assign_out[P.units[i].box] = P.unit_worker[i];
     }

@@ -37,6 +37,7 @@ __global__ void b_half_kernel(const SimDev* __restrict__ sims, const int* __rest
         int i = (int)(c % nx);
         int j = (int)((c / nx) % ny);
         int k = (int)(c / ((int64_t)nx * ny));
+        if (!cell_owned(S, i, j, k)) continue;
         int64_t o = pidx(S, i, j, k);
         int64_t oi = pidx(S, nxt(i, nx), j, k);
         int64_t oj = (DIM == 3) ? pidx(S, i, nxt(j, ny), k) : o;
@@ -87,6 +88,7 @@ __global__ void e_kernel(const SimDev* __restrict__ sims, const int* __restrict_
         int i = (int)(c % nx);
         int j = (int)((c / nx) % ny);
         int k = (int)(c / ((int64_t)nx * ny));
+        if (!cell_owned(S, i, j, k)) continue;
         int64_t o = pidx(S, i, j, k);
         int64_t oi = pidx(S, prv(i, nx), j, k);
         int64_t oj = (DIM == 3) ? pidx(S, i, prv(j, ny), k) : o;
@@ -122,6 +124,7 @@ __global__ void damp_kernel(const SimDev* __restrict__ sims, const int* __restri
         int64_t r = c - (int64_t)layer * per_layer;
         int i = (int)(r % nx), j = (int)(r / nx);
         int k = layer < A ? layer : nz - 2 * A + layer;
+        if (!cell_owned(S, i, j, k)) continue;
         int p = k < A ? A - k : k - (nz - 1 - A);
         double q = (double)p / (double)A;
         double f = 1.0 - 0.5 * q * q;
@@ -296,6 +299,31 @@ cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t 
         damp_kernel<<<blocks_for(t, 256), 256, 0, st>>>(dsim, nullptr);
     }
     return pic_launch_guards(dsim, h, 0, 6, st);
+}
+
+cudaError_t pic_launch_fold(const SimDev* dsim, const SimDev& h, cudaStream_t st) {
+    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
+    fold_j_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_field_stage(const SimDev* dsim, const SimDev& h, int stage, cudaStream_t st) {
+    const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
+    const int nb = blocks_for(ncell, 256);
+    if (stage == 0 || stage == 2) {
+        if (h.dim == 3) b_half_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
+        else b_half_kernel<2><<<nb, 256, 0, st>>>(dsim, nullptr);
+        if (stage == 2 && h.absorb > 0) {
+            int64_t t = (int64_t)h.n[0] * h.n[1] * 2 * h.absorb;
+            damp_kernel<<<blocks_for(t, 256), 256, 0, st>>>(dsim, nullptr);
+        }
+    } else if (stage == 1) {
+        if (h.dim == 3) e_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
+        else e_kernel<2><<<nb, 256, 0, st>>>(dsim, nullptr);
+    } else {
+        return pic_launch_guards(dsim, h, 0, 6, st);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& h, int c0, int nc,

@@ -87,6 +87,8 @@ struct SimDev {
     uint64_t* cost_time;  // [nboxes] summed %globaltimer ns of the box's units (kernel-time cost)
     int64_t* step;        // device step counter
     int32_t* err;         // device error word (shared with the schedule)
+    const int32_t* owner; // box sharding: rank owning each box (nullptr: every box is this rank's)
+    int rank;             // this simulation's rank when sharded
     LaserDev las;
     SpeciesDev sp[PIC_MAXSP];
 };
@@ -106,6 +108,14 @@ struct SchedDev {
 // padded linear index of interior cell (i,j,k) of a simulation
 __host__ __device__ inline int64_t pidx(const SimDev& s, int i, int j, int k) {
     return ((int64_t)(k + s.g[2]) * s.pn[1] + (j + s.g[1])) * s.pn[0] + (i + s.g[0]);
+}
+
+// whether interior cell (i,j,k) lies in a box this simulation owns (always
+// when it is not sharded)
+__host__ __device__ inline bool cell_owned(const SimDev& s, int i, int j, int k) {
+    if (!s.owner) return true;
+    const int b = ((k / s.bsz[2]) * s.nb[1] + (j / s.bsz[1])) * s.nb[0] + (i / s.bsz[0]);
+    return s.owner[b] == s.rank;
 }
 
 // streaming multiprocessors of the current device, queried once per device
@@ -158,6 +168,15 @@ cudaError_t pic_launch_pad(const double* dense, double* padded, const SimDev& hs
                            cudaStream_t st);
 cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& hsim, int first_comp,
                               int ncomp, cudaStream_t st);
+// the field update in its sub-steps, for sharded runs that exchange ghost
+// cells between them: 0 B half step, 1 E step (with J and the antenna),
+// 2 B half step and damping layers, 3 periodic guard fill; and the fold of
+// guard-cell current into the domain
+cudaError_t pic_launch_field_stage(const SimDev* dsim, const SimDev& hsim, int stage, cudaStream_t st);
+cudaError_t pic_launch_fold(const SimDev* dsim, const SimDev& hsim, cudaStream_t st);
+// keys and histogram of particles [p0, p1) of species sp from their positions
+cudaError_t pic_launch_keys_range(const SimDev* dsim, const SimDev& hsim, int sp, int64_t p0, int64_t p1,
+                                  cudaStream_t st);
 // multi-simulation launches over a device list of slots (blockIdx.y = slot)
 cudaError_t pic_launch_fields_multi(const SimDev* sims, const int* slots, int nslots, int dim,
                                     int64_t max_cells, int64_t max_padded, bool any_absorb,

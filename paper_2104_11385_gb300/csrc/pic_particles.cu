@@ -145,6 +145,23 @@ __global__ void pic_initial_keys_kernel(SimDev* __restrict__ sims, int sp_idx, i
     }
 }
 
+template <int DIM>
+__global__ void pic_keys_range_kernel(SimDev* __restrict__ sims, int sp_idx, int64_t p0, int64_t p1) {
+    const SimDev& S = sims[0];
+    const SpeciesDev& sp = S.sp[sp_idx];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q0 = p0 + (int64_t)blockIdx.x * blockDim.x; q0 < p1; q0 += stride) {
+        const int64_t p = q0 + threadIdx.x;
+        if (p >= p1) break;
+        int ix = min(max(__double2int_rd(sp.cur[0][p]), 0), S.n[0] - 1);
+        int iy = (DIM == 3) ? min(max(__double2int_rd(sp.cur[1][p]), 0), S.n[1] - 1) : 0;
+        int iz = min(max(__double2int_rd(sp.cur[2][p]), 0), S.n[2] - 1);
+        int key = tile_key(S, ix, iy, iz);
+        sp.key[p] = key;
+        warp_hist_add(sp.count, key);
+    }
+}
+
 __global__ void pic_box_counts_kernel(const SimDev* __restrict__ sims, int64_t* out) {
     const SimDev& S = sims[0];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < S.nboxes; b += gridDim.x * blockDim.x) {
@@ -267,6 +284,16 @@ cudaError_t pic_launch_initial_keys(const SimDev* dsim, const SimDev& hsim, int 
     if (np > 0) {
         if (hsim.dim == 3) pic_initial_keys_kernel<3><<<grid_for(np, 256), 256, 0, st>>>(d, sp, np);
         else pic_initial_keys_kernel<2><<<grid_for(np, 256), 256, 0, st>>>(d, sp, np);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pic_launch_keys_range(const SimDev* dsim, const SimDev& hsim, int sp, int64_t p0, int64_t p1,
+                                  cudaStream_t st) {
+    SimDev* d = const_cast<SimDev*>(dsim);
+    if (p1 > p0) {
+        if (hsim.dim == 3) pic_keys_range_kernel<3><<<grid_for(p1 - p0, 256), 256, 0, st>>>(d, sp, p0, p1);
+        else pic_keys_range_kernel<2><<<grid_for(p1 - p0, 256), 256, 0, st>>>(d, sp, p0, p1);
     }
     return cudaGetLastError();
 }

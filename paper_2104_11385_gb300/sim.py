@@ -226,6 +226,47 @@ class Simulation:
         self._check(self._lib.pic_autotune(self._h, int(steps_per_candidate), ctypes.byref(c)))
         return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "split": c.split, "tile": c.tile, "ppt": c.ppt}
 
+    # ---- box sharding (include/pic_shard.h); device tensors for buffers
+    def shard_set_owner(self, owner, rank):
+        o = np.ascontiguousarray(owner, np.int32)
+        self._check(self._lib.pic_shard_set_owner(self._h, o.ctypes.data_as(L._pi32), int(rank)))
+
+    def shard_pack(self, first_comp, ncomp, cells, buf):
+        self._check(self._lib.pic_shard_pack(self._h, int(first_comp), int(ncomp), ctypes.c_void_p(cells.data_ptr()),
+                                             int(cells.numel()), ctypes.c_void_p(buf.data_ptr())))
+
+    def shard_unpack(self, first_comp, ncomp, cells, buf, add):
+        self._check(self._lib.pic_shard_unpack(self._h, int(first_comp), int(ncomp),
+                                               ctypes.c_void_p(cells.data_ptr()), int(cells.numel()),
+                                               ctypes.c_void_p(buf.data_ptr()), 1 if add else 0))
+
+    def shard_push(self):
+        self._check(self._lib.pic_shard_push(self._h))
+
+    def shard_field_stage(self, stage):
+        self._check(self._lib.pic_shard_field_stage(self._h, int(stage)))
+
+    def shard_rekey(self):
+        self._check(self._lib.pic_shard_rekey(self._h))
+
+    def shard_take_leaving(self, species, nranks):
+        c = np.zeros(int(nranks), np.int64)
+        self._check(self._lib.pic_shard_take_leaving(self._h, int(species), int(nranks), c.ctypes.data_as(L._pi64)))
+        return c
+
+    def shard_read_leaving(self, species, dst, soa, ids):
+        ptrs = (ctypes.c_void_p * 7)(*[ctypes.c_void_p(t.data_ptr()) for t in soa])
+        self._check(self._lib.pic_shard_read_leaving(self._h, int(species), int(dst), ptrs,
+                                                     ctypes.c_void_p(ids.data_ptr())))
+
+    def shard_add_arriving(self, species, soa, ids):
+        ptrs = (ctypes.c_void_p * 7)(*[ctypes.c_void_p(t.data_ptr()) for t in soa])
+        self._check(self._lib.pic_shard_add_arriving(self._h, int(species), int(ids.numel()), ptrs,
+                                                     ctypes.c_void_p(ids.data_ptr())))
+
+    def shard_finish(self, advance=True):
+        self._check(self._lib.pic_shard_finish(self._h, 1 if advance else 0))
+
     def set_profiling(self, on=True):
         self._check(self._lib.pic_set_profiling(self._h, 1 if on else 0))
 
@@ -264,6 +305,35 @@ def lb_efficiency(costs, assign, n_workers) -> float:
     L.check(lib.pic_lb_efficiency(c.ctypes.data_as(L._pd), a.ctypes.data_as(L._pi32), c.size,
                                   int(n_workers), ctypes.byref(e)))
     return e.value
+
+
+def shard_halo_cells(dim, ncell, box, owner, own, near, halo) -> np.ndarray:
+    """pic_shard_halo_cells: cells of `own`'s boxes within `halo` of `near`'s boxes (host, no GPU)."""
+    lib = L.load()
+    g = grid_desc(dim, ncell, box, (1.0, 1.0, 1.0))
+    o = np.ascontiguousarray(owner, np.int32)
+    n = ctypes.c_int64()
+    L.check(lib.pic_shard_halo_cells(ctypes.byref(g), o.ctypes.data_as(L._pi32), int(own), int(near), int(halo),
+                                     None, ctypes.byref(n)))
+    out = np.empty(n.value, np.int64)
+    L.check(lib.pic_shard_halo_cells(ctypes.byref(g), o.ctypes.data_as(L._pi32), int(own), int(near), int(halo),
+                                     out.ctypes.data_as(L._pi64), ctypes.byref(n)))
+    return out
+
+
+def shard_moved_cells(dim, ncell, box, old_owner, new_owner, src, dst) -> np.ndarray:
+    """pic_shard_moved_cells: cells of the boxes moving from rank src to rank dst (host, no GPU)."""
+    lib = L.load()
+    g = grid_desc(dim, ncell, box, (1.0, 1.0, 1.0))
+    a = np.ascontiguousarray(old_owner, np.int32)
+    b = np.ascontiguousarray(new_owner, np.int32)
+    n = ctypes.c_int64()
+    L.check(lib.pic_shard_moved_cells(ctypes.byref(g), a.ctypes.data_as(L._pi32), b.ctypes.data_as(L._pi32),
+                                      int(src), int(dst), None, ctypes.byref(n)))
+    out = np.empty(n.value, np.int64)
+    L.check(lib.pic_shard_moved_cells(ctypes.byref(g), a.ctypes.data_as(L._pi32), b.ctypes.data_as(L._pi32),
+                                      int(src), int(dst), out.ctypes.data_as(L._pi64), ctypes.byref(n)))
+    return out
 
 
 def grid_desc(dim, ncell, box, dx, stream=None) -> L.GridDesc:

@@ -650,7 +650,7 @@ int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, i
         ntiles *= nb * (T > 0 ? g->box[a] / T : 1);
     }
     auto r = [](int64_t n, int64_t sz) { return std::max<int64_t>(n, 1) * sz; };
-    int64_t b = r(pvol * PIC_NCOMP, 8) + 2 * r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) +
+    int64_t b = r(pvol * PIC_NCOMP, 8) + 2 * r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) + (int64_t)pic_ring_bytes(pic_sm_count()) +
                 (int64_t)sizeof(SchedDev) + r(8193, 4) + r(8192, 4) + r(2, 4) + r(4, 8) + r(nboxes, 8);
     for (int i = 0; i < nsp; ++i) {
         const int64_t cap = std::max<int64_t>(np[i], 1);
@@ -774,6 +774,7 @@ pic_status pic_init(const pic_grid_desc* desc, pic_sim** out) {
         (st = dalloc(s, &h.err, 1)) != PIC_OK || (st = dalloc(s, &s->d, 1)) != PIC_OK ||
         (st = dalloc(s, &s->ds, 1)) != PIC_OK || (st = dalloc(s, &s->hs.list_off, 8193)) != PIC_OK ||
         (st = dalloc(s, &s->hs.head, 8192)) != PIC_OK || (st = dalloc(s, &s->hs.meta, 2)) != PIC_OK ||
+        (st = dalloc(s, &s->hs.rings, pic_ring_bytes(s->nsm) / sizeof(double))) != PIC_OK ||
         (st = dalloc(s, &s->d_scalar, 4)) != PIC_OK || (st = dalloc(s, &s->d_box_np, h.nboxes)) != PIC_OK) {
         g_last_error = s->err;
         pic_destroy(s);
@@ -1216,7 +1217,7 @@ pic_status pic_set_launch(pic_sim* s, const pic_launch_cfg* cfg) {
         s->threads = cfg->threads;
     }
     if (cfg->ctas_per_sm > 0) {
-        if (cfg->ctas_per_sm > 4) return fail(s, PIC_EINVAL, "ctas_per_sm must be 1..4");
+        if (cfg->ctas_per_sm > PIC_RING_CTAS_PER_SM) return fail(s, PIC_EINVAL, "ctas_per_sm must be 1..4");
         s->ctas_per_sm = cfg->ctas_per_sm;
     }
     const int old_split = s->split;

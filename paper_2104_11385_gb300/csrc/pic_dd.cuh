@@ -190,7 +190,17 @@ template <>
 struct Arith<double> {
     __device__ static __forceinline__ double from(double x) { return x; }
     __device__ static __forceinline__ double to(double x) { return x; }
-    __device__ static __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+    // 1/sqrt(x) for x >= 1 (1 + |u|^2): the hardware estimate refined by two
+    // Newton-Raphson steps y <- y + y (1/2 - (x/2) y^2), each squaring the
+    // relative error, to about 1 ulp
+    __device__ static __forceinline__ double rsqrt(double x) {
+        double y;
+        asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+        const double hx = 0.5 * x;
+        y = ::fma(y, ::fma(-hx * y, y, 0.5), y);
+        y = ::fma(y, ::fma(-hx * y, y, 0.5), y);
+        return y;
+    }
     __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
     // 2/x for x >= 1: the hardware reciprocal estimate refined by two
     // Newton-Raphson steps (e = 1 - x y, y <- y + y e; each squares the

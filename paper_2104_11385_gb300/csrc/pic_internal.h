@@ -103,7 +103,17 @@ struct SchedDev {
     int32_t* head;        // [nlists] atomic pull counters
     int32_t* meta;        // [0] = nlists, [1] = steal (0/1)
     int32_t* err;         // device error word
+    double* rings;        // [PIC_RING_CTAS_PER_SM x SMs x 8 warps x PIC_RING_DOUBLES] rings of
+                          // cell-crossing particles in global memory (FP64, float-float)
 };
+
+// global ring scratch: per warp 7 fields x 64 slots of doubles, for up to 4
+// persistent CTAs per SM of up to 8 warps
+#define PIC_RING_DOUBLES (7 * 64)
+#define PIC_RING_CTAS_PER_SM 4
+__host__ inline size_t pic_ring_bytes(int nsm) {
+    return (size_t)nsm * PIC_RING_CTAS_PER_SM * 8 * PIC_RING_DOUBLES * sizeof(double);
+}
 
 // padded linear index of interior cell (i,j,k) of a simulation
 __host__ __device__ inline int64_t pidx(const SimDev& s, int i, int j, int k) {

@@ -255,12 +255,36 @@ struct EBHalo {
 };
 
 // interpolation of one component from a shared tile with extents (SX, SY);
-// the tile holds R values (doubles, or float pairs converted in place)
+// the tile holds R values (doubles, or float pairs converted in place).  D,
+// when given (linear FP64), holds the tile's x differences F[x+1] - F[x] on
+// rows of SX - 1, so that each x lerp is one FMA.
 template <class R, int ORDER, int DIM>
 __device__ __forceinline__ R interp(const R* __restrict__ F, int SX, int SY, const Support<ORDER, R>& sx,
-                                    const Support<ORDER, R>& sy, const Support<ORDER, R>& sz) {
+                                    const Support<ORDER, R>& sy, const Support<ORDER, R>& sz,
+                                    const R* __restrict__ D = nullptr) {
     // tile column 0 is local cell -EBHalo<ORDER>::lo
     constexpr int H = EBHalo<ORDER>::lo;
+    if constexpr (ORDER == 1 && std::is_same<R, double>::value) {
+        if (D) {
+            auto lerp = [](R a, R b, R f) { return fma(f, b - a, a); };
+            const R fx = sx.w[1];
+            const int DX = SX - 1;
+            if constexpr (DIM == 3) {
+                const int r00 = (sz.s + H) * SY + (sy.s + H);
+                const int x = sx.s + H;
+                const R a00 = fma(fx, D[r00 * DX + x], F[r00 * SX + x]);
+                const R a10 = fma(fx, D[(r00 + 1) * DX + x], F[(r00 + 1) * SX + x]);
+                const R a01 = fma(fx, D[(r00 + SY) * DX + x], F[(r00 + SY) * SX + x]);
+                const R a11 = fma(fx, D[(r00 + SY + 1) * DX + x], F[(r00 + SY + 1) * SX + x]);
+                return lerp(lerp(a00, a10, sy.w[1]), lerp(a01, a11, sy.w[1]), sz.w[1]);
+            } else {
+                const int r0 = sz.s + H, x = sx.s + H;
+                const R a0 = fma(fx, D[r0 * DX + x], F[r0 * SX + x]);
+                const R a1 = fma(fx, D[(r0 + 1) * DX + x], F[(r0 + 1) * SX + x]);
+                return lerp(a0, a1, sz.w[1]);
+            }
+        }
+    }
     if constexpr (ORDER == 1) {
         // linear: nested lerps a + f (b - a) need only the fractional parts
         auto lerp = [](R a, R b, R f) { return fma(f, b - a, a); };
@@ -321,14 +345,15 @@ __device__ __forceinline__ T pick3(int a, const T& v0, const T& v1, const T& v2)
 template <class R, int ORDER, int DIM>
 __device__ __forceinline__ void gather6(const R* __restrict__ sEB, int stride, int SX, int SY,
                                         const Support<ORDER, R>* nd, const Support<ORDER, R>* hf, R* e,
-                                        R* b) {
+                                        R* b, const R* __restrict__ sD = nullptr, int dstride = 0) {
     if constexpr (!std::is_same<R, dd>::value) {
-        e[0] = interp<R, ORDER, DIM>(sEB, SX, SY, hf[0], nd[1], nd[2]);
-        e[1] = interp<R, ORDER, DIM>(sEB + stride, SX, SY, nd[0], hf[1], nd[2]);
-        e[2] = interp<R, ORDER, DIM>(sEB + 2 * stride, SX, SY, nd[0], nd[1], hf[2]);
-        b[0] = interp<R, ORDER, DIM>(sEB + 3 * stride, SX, SY, nd[0], hf[1], hf[2]);
-        b[1] = interp<R, ORDER, DIM>(sEB + 4 * stride, SX, SY, hf[0], nd[1], hf[2]);
-        b[2] = interp<R, ORDER, DIM>(sEB + 5 * stride, SX, SY, hf[0], hf[1], nd[2]);
+        const bool hd = sD != nullptr;
+        e[0] = interp<R, ORDER, DIM>(sEB, SX, SY, hf[0], nd[1], nd[2], hd ? sD : nullptr);
+        e[1] = interp<R, ORDER, DIM>(sEB + stride, SX, SY, nd[0], hf[1], nd[2], hd ? sD + dstride : nullptr);
+        e[2] = interp<R, ORDER, DIM>(sEB + 2 * stride, SX, SY, nd[0], nd[1], hf[2], hd ? sD + 2 * dstride : nullptr);
+        b[0] = interp<R, ORDER, DIM>(sEB + 3 * stride, SX, SY, nd[0], hf[1], hf[2], hd ? sD + 3 * dstride : nullptr);
+        b[1] = interp<R, ORDER, DIM>(sEB + 4 * stride, SX, SY, hf[0], nd[1], hf[2], hd ? sD + 4 * dstride : nullptr);
+        b[2] = interp<R, ORDER, DIM>(sEB + 5 * stride, SX, SY, hf[0], hf[1], nd[2], hd ? sD + 5 * dstride : nullptr);
     } else {
         R v0 = Arith<R>::c(0.0), v1 = v0, v2 = v0, v3 = v0, v4 = v0, v5 = v0;
 #pragma unroll 1
@@ -429,24 +454,35 @@ struct QFields {
     static constexpr int n = DIM == 3 ? 7 : 6;
 };
 
+static_assert(QFields<3>::n * WQ == PIC_RING_DOUBLES && QMAXWARPS == 8,
+              "a warp's global ring holds 7 fields of WQ slots; rings are allocated for 8 warps per CTA");
+
 struct SmemPlan {
     int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
+    int d_stride;   // doubles per component of the x-difference tile (0: none)
     int j_stride;   // doubles per J component
-    int eb_vol, j_vol;
+    int eb_vol, d_vol, j_vol;
     size_t bytes;
 };
 
 // jshared: the J tile lives in shared memory (FP32 variant); otherwise the
-// current goes to global memory and the J region is empty
-__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared) {
+// current goes to global memory and the J region is empty.  xdiff: the x
+// differences of the staged E/B tile are kept beside it (linear FP64).
+// Layout: E/B tile | x differences | J tile | (FP32 variant) rings.
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared, bool xdiff = false) {
     SmemPlan p;
     p.eb_vol = ebs[0] * ebs[1] * ebs[2];
+    p.d_vol = xdiff ? (ebs[0] - 1) * ebs[1] * ebs[2] : 0;
     p.j_vol = jshared ? js[0] * js[1] * js[2] : 0;
     p.eb_stride = (p.eb_vol + 15) & ~15;
+    p.d_stride = (p.d_vol + 15) & ~15;
     p.j_stride = (p.j_vol + 1) & ~1;
-    p.bytes = (size_t)(6 * p.eb_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
+    p.bytes = (size_t)(6 * p.eb_stride + 6 * p.d_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
     return p;
 }
+
+// whether a precision / shape order keeps the x-difference tile: FP64 linear
+__host__ __device__ inline bool uses_xdiff(int prec, int order) { return prec == 0 && order == 1; }
 
 template <int DIM, int ORDER, class JT>
 __device__ void flush_j(const SimDev& S, const Tile& tl, const JT* __restrict__ sJ,
@@ -809,7 +845,8 @@ __device__ __forceinline__ PIn load_one(const SpeciesDev& sp, int64_t p) {
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
 template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
-                                         const R* __restrict__ sEB, const JView<typename JAcc<R>::type>& V,
+                                         const R* __restrict__ sEB, const R* __restrict__ sD,
+                                         const JView<typename JAcc<R>::type>& V,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                          const R* jf, const R* dtd, R kq, R qs, int64_t p, const PIn& in,
                                          int32_t* err) {
@@ -846,7 +883,7 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     }
     const int SX = S.ebs[0], SY = S.ebs[1];
     R ev[3], bv[3];
-    gather6<R, ORDER, DIM>(sEB, P.eb_stride, SX, SY, nd, hf, ev, bv);
+    gather6<R, ORDER, DIM>(sEB, P.eb_stride, SX, SY, nd, hf, ev, bv, sD, P.d_stride);
     const R e0 = ev[0], e1 = ev[1], e2 = ev[2], b0 = bv[0], b1 = bv[1], b2 = bv[2];
 
     // ---- relativistic Boris push
@@ -858,12 +895,13 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     const R t2n = fma(t2, t2, fma(t1, t1, t0 * t0));
     const R sf = A::two_over(one + t2n);
     const R s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
-    const R d0 = m0 + (m1 * t2 - m2 * t1);
-    const R d1 = m1 + (m2 * t0 - m0 * t2);
-    const R d2 = m2 + (m0 * t1 - m1 * t0);
-    const R p0 = m0 + (d1 * s2 - d2 * s1);
-    const R p1 = m1 + (d2 * s0 - d0 * s2);
-    const R p2 = m2 + (d0 * s1 - d1 * s0);
+    // u' = u- + u- x t, u+ = u- + u' x s, each component as two FMAs
+    const R d0 = fma(m1, t2, fma(-m2, t1, m0));
+    const R d1 = fma(m2, t0, fma(-m0, t2, m1));
+    const R d2 = fma(m0, t1, fma(-m1, t0, m2));
+    const R p0 = fma(d1, s2, fma(-d2, s1, m0));
+    const R p1 = fma(d2, s0, fma(-d0, s2, m1));
+    const R p2 = fma(d0, s1, fma(-d1, s0, m2));
     const R n0 = fma(kq, e0, p0), n1 = fma(kq, e1, p1), n2 = fma(kq, e2, p2);
     const R ign = A::rsqrt(fma(n2, n2, fma(n1, n1, fma(n0, n0, one))));
     const R v1 = n1 * ign;
@@ -1045,6 +1083,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     using A = Arith<R>;
     using JT = typename JAcc<R>::type;
     constexpr bool GJ = JAcc<R>::global;
+    constexpr bool XD = PREC == 0 && ORDER == 1;  // x-difference tile beside the E/B tile
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -1071,6 +1110,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     cur.t = -1;
     int visited = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ring of cell-crossing particles: global scratch with the global J
+    // target (FP64, float-float), shared memory after the J tile otherwise
+    double* const gring = GJ ? sd->rings + ((size_t)blockIdx.x * QMAXWARPS + warp) * PIC_RING_DOUBLES : nullptr;
 
     // global J target: a warp's ring of cell-crossing particles outlives tile
     // changes; it is drained when the simulation changes (rings hold one
@@ -1079,10 +1121,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         if constexpr (GJ) {
             const unsigned head = s_qhead[warp], tail = s_qtail[warp];
             if (tail != head) {
-                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false);
+                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false, XD);
                 const SimConsts<R, DIM> K(CS);
-                double* sQw = smem + 6 * CP.eb_stride + warp * (QFields<DIM>::n * WQ);
-                drain<R, DIM, ORDER>(CS, cur, j_view<JT>(CS, cur, nullptr, CP), sQw, head, tail - head, K.jf,
+                drain<R, DIM, ORDER>(CS, cur, j_view<JT>(CS, cur, nullptr, CP), gring, head, tail - head, K.jf,
                                      sd->err);
                 __syncwarp();
                 if (lane == 0) s_qhead[warp] = tail;
@@ -1112,10 +1153,11 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         const SimDev& S = sims[unit.sim];
         const bool cap_clk = (S.capture & 1) != 0, cap_time = (S.capture & 2) != 0;
         const uint64_t t_unit0 = (threadIdx.x == 0 && cap_time) ? globaltimer() : 0ull;
-        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ);
+        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ, XD);
         double* sEBd = smem;
         const R* sEB = reinterpret_cast<const R*>(smem);
-        double* sJd = smem + 6 * P.eb_stride;  // J tile (FP32 variant only); the rings follow it
+        double* sDd = smem + 6 * P.eb_stride;   // x differences (linear FP64)
+        double* sJd = sDd + 6 * P.d_stride;     // J tile (FP32 variant only); its rings follow it
         JT* sJ = reinterpret_cast<JT*>(sJd);
         unsigned long long my_clk = 0ull;
         const SimConsts<R, DIM> K(S);
@@ -1139,8 +1181,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     if constexpr (!GJ) {
                         if (cur.t >= 0) {
                             const SimDev& CS = sims[cur.sim];
-                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true);
-                            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride), CP);
+                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD);
+                            flush_j<DIM, ORDER>(CS, cur,
+                                                reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
                             __syncthreads();
                         }
                     }
@@ -1172,6 +1215,17 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase ^ 1u);
                         __syncthreads();
                         return;
+                    }
+                    if constexpr (XD) {
+                        // x differences of every staged row: each x lerp of the gather becomes one FMA
+                        const int SXd = S.ebs[0] - 1;
+                        for (int i = threadIdx.x; i < 6 * P.d_vol; i += blockDim.x) {
+                            const int c = i / P.d_vol, r = i - c * P.d_vol;
+                            const int row = r / SXd, x = r - row * SXd;
+                            const double* f = sEBd + c * P.eb_stride + row * S.ebs[0] + x;
+                            sDd[c * P.d_stride + r] = f[1] - f[0];
+                        }
+                        __syncthreads();
                     }
                     if constexpr (PREC == 1) {
                         // E/B tile to float pairs, in place (8 bytes either way)
@@ -1210,7 +1264,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 {
                     // per-warp loop: no CTA barrier until the tile changes
                     const JView<JT> V = j_view<JT>(S, cur, sJ, P);
-                    double* sQw = sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
+                    double* sQw = GJ ? gring : sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
+                    const R* sD = XD ? reinterpret_cast<const R*>(sDd) : nullptr;
                     volatile unsigned* vtail = s_qtail + warp;
                     for (int64_t p0 = s0 + warp * (32 * PPT); p0 < s1; p0 += (int64_t)blockDim.x * PPT) {
                         PIn in[PPT];
@@ -1223,8 +1278,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         for (int q = 0; q < PPT; ++q) {
                             const int64_t p = p0 + q * 32 + lane;
                             if (p < s1)
-                                push_one<R, DIM, ORDER>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq,
-                                                        qs, p, in[q], sd->err);
+                                push_one<R, DIM, ORDER>(S, sp, cur, sEB, sD, V, sQw, s_qtail + warp, P, K.jf, K.dtd,
+                                                        kq, qs, p, in[q], sd->err);
                             __syncwarp();
                             const unsigned head = s_qhead[warp], tail = *vtail;
                             if (tail - head >= 32u) {
@@ -1271,8 +1326,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         } else {
             __syncthreads();
             const SimDev& CS = sims[cur.sim];
-            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true);
-            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride), CP);
+            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD);
+            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
         }
     }
 }

@@ -315,7 +315,8 @@ pic_status pic_server_create(const pic_server_desc* d, pic_server** out) {
               cudaMalloc(&s->hs.list_off, 2 * sizeof(int32_t)) == cudaSuccess &&
               cudaMalloc(&s->hs.head, sizeof(int32_t)) == cudaSuccess &&
               cudaMalloc(&s->hs.meta, 2 * sizeof(int32_t)) == cudaSuccess &&
-              cudaMalloc(&s->hs.err, sizeof(int32_t)) == cudaSuccess;
+              cudaMalloc(&s->hs.err, sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc(&s->hs.rings, pic_ring_bytes(s->nsm)) == cudaSuccess;
     if (!ok) {
         pic_server_destroy(s);
         return pic_record_error(PIC_ENOMEM, "server allocation failed");
@@ -566,6 +567,7 @@ pic_status pic_server_destroy(pic_server* s) {
     cudaFree(s->hs.head);
     cudaFree(s->hs.meta);
     cudaFree(s->hs.err);
+    cudaFree(s->hs.rings);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return PIC_OK;

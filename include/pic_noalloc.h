@@ -29,7 +29,9 @@ extern "C" {
  *     message in pic_last_error(NULL); nothing is launched.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     before any stream capture begins.  The address is kept per device and
+ *     CUDA context: after a device reset (cudaDeviceReset) the next call looks
+ *     it up again, so that call too belongs outside a capture.
  *   - Every call, on every stream, shares the one array, and it keeps the last
  *     call's contents; each call zeroes the part it uses on its stream first.
  *     Calls whose device work overlaps (different streams, or host threads

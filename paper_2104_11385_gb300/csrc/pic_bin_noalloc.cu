@@ -8,6 +8,7 @@
 // latency-critical loops that must not hit the allocator.  They pass their own
 // input and output buffers; the only scratch the binning needs, one cursor per
 // box, lives in a fixed file-scope device array instead.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -24,11 +25,40 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
+void* g_scratch_ptr[kMaxDevices] = {};            // device address of the array, per device
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // id of the context it was looked up in
 thread_local std::string g_err;
 
+// Id of the current context (0 when the driver cannot tell): a device reset
+// destroys the primary context and the module with the array, so an address
+// looked up in an earlier context must not be reused.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext*);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrentFn)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetIdFn)p;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
 // The array's name is a host-side stand-in in host code, not a device
-// address: look the address up once per device, with that device current.
+// address: look the address up once per device and context, with that device
+// current.
 pic_status scratch_for_current_device(int32_t** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -36,7 +66,11 @@ pic_status scratch_for_current_device(int32_t** out) {
         g_err = "no usable current CUDA device";
         return PIC_ECUDA;
     }
+    // (before the first runtime call that creates the context the id reads 0;
+    // the next call then finds a new id and looks the address up once more)
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_ptr[dev] && ctx != g_scratch_ctx[dev]) g_scratch_ptr[dev] = nullptr;
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_bin_cursor_scratch);
@@ -47,6 +81,7 @@ pic_status scratch_for_current_device(int32_t** out) {
             return PIC_ECUDA;
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<int32_t*>(g_scratch_ptr[dev]);
     return PIC_OK;

@@ -1217,13 +1217,19 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         return;
                     }
                     if constexpr (XD) {
-                        // x differences of every staged row: each x lerp of the gather becomes one FMA
-                        const int SXd = S.ebs[0] - 1;
-                        for (int i = threadIdx.x; i < 6 * P.d_vol; i += blockDim.x) {
-                            const int c = i / P.d_vol, r = i - c * P.d_vol;
-                            const int row = r / SXd, x = r - row * SXd;
-                            const double* f = sEBd + c * P.eb_stride + row * S.ebs[0] + x;
-                            sDd[c * P.d_stride + r] = f[1] - f[0];
+                        // x differences of every staged row (each x lerp of the gather
+                        // becomes one FMA): one thread per row, walking along x
+                        const int SX = S.ebs[0], rows = S.ebs[1] * S.ebs[2];
+                        for (int i = threadIdx.x; i < 6 * rows; i += blockDim.x) {
+                            const int c = i / rows, row = i - c * rows;
+                            const double* f = sEBd + c * P.eb_stride + row * SX;
+                            double* dst = sDd + c * P.d_stride + row * (SX - 1);
+                            double prev = f[0];
+                            for (int x = 1; x < SX; ++x) {
+                                const double v = f[x];
+                                dst[x - 1] = v - prev;
+                                prev = v;
+                            }
                         }
                         __syncthreads();
                     }

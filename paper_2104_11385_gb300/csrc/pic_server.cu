@@ -168,10 +168,20 @@ pic_status admit(pic_server* s, Request& r, int slot) {
     if (r.desc.nspecies == 0) {
         const pic_plasma_init& pl = r.desc.plasma;
         const int64_t np = g.ncell[0] * g.ncell[1] * g.ncell[2] * (int64_t)pl.ppc;
-        double* buf = nullptr;
-        int64_t* ids = nullptr;
-        SCU(s, cudaMallocAsync((void**)&buf, (size_t)std::max<int64_t>(np, 1) * 7 * sizeof(double), s->stream));
-        SCU(s, cudaMallocAsync((void**)&ids, (size_t)std::max<int64_t>(np, 1) * sizeof(int64_t), s->stream));
+        // the loader's staging buffers are freed (stream-ordered) on every way out
+        struct Staging {
+            cudaStream_t st;
+            double* buf = nullptr;
+            int64_t* ids = nullptr;
+            ~Staging() {
+                if (buf) cudaFreeAsync(buf, st);
+                if (ids) cudaFreeAsync(ids, st);
+            }
+        } stg{s->stream};
+        SCU(s, cudaMallocAsync((void**)&stg.buf, (size_t)std::max<int64_t>(np, 1) * 7 * sizeof(double), s->stream));
+        SCU(s, cudaMallocAsync((void**)&stg.ids, (size_t)std::max<int64_t>(np, 1) * sizeof(int64_t), s->stream));
+        double* buf = stg.buf;
+        int64_t* ids = stg.ids;
         if (np > 0) {
             int64_t nb = std::min<int64_t>((np + 255) / 256, (int64_t)s->nsm * 32);
             plasma_init_kernel<<<(int)nb, 256, 0, s->stream>>>(
@@ -185,8 +195,6 @@ pic_status admit(pic_server* s, Request& r, int slot) {
         for (int a = 0; a < 7; ++a) soa[a] = buf + a * np;
         int spid = 0;
         st = pic_add_species(sim, -1.0, 1.0, np, soa, ids, 1, &spid);
-        cudaFreeAsync(buf, s->stream);
-        cudaFreeAsync(ids, s->stream);
         if (st != PIC_OK) return sfail(s, st, std::string("request species: ") + pic_last_error(sim));
         pic_add_background(sim, pl.density);
     } else {
@@ -206,8 +214,12 @@ pic_status admit(pic_server* s, Request& r, int slot) {
     if (st != PIC_OK) return sfail(s, st, std::string("request mirror: ") + pic_internal_error(sim));
     SCU(s, cudaMemcpyAsync(s->d_sims + slot, &mirror, sizeof(SimDev), cudaMemcpyHostToDevice, s->stream));
     SCU(s, cudaStreamSynchronize(s->stream));
+    // admission reserved the estimate; the budget holds for the actual bytes
+    const int64_t actual = pic_internal_bytes(sim);
+    if (s->bytes_in_use + actual > s->desc.hbm_budget_bytes)
+        return sfail(s, PIC_ENOMEM, "request footprint " + std::to_string(actual) + " bytes exceeds the HBM budget");
     pic_internal_mark_external(sim);
-    r.footprint = pic_internal_bytes(sim);
+    r.footprint = actual;
     r.slot = slot;
     r.state = PIC_REQ_ACTIVE;
     r.t_admit = now_s();
@@ -349,7 +361,12 @@ pic_status pic_server_submit(pic_server* s, const pic_request_desc* d, int64_t* 
     int64_t per[4] = {0, 0, 0, 0};
     int nsp = 0;
     r.nparticles = request_particles(*d, per, &nsp);
-    r.footprint = pic_internal_estimate_bytes(&g, per, nsp);
+    // the grid as admission will create it: the server's shape order (it sets
+    // the guard widths), no absorbing layers
+    pic_grid_desc ga = g;
+    ga.shape_order = s->desc.shape_order;
+    ga.absorb_cells = 0;
+    r.footprint = pic_internal_estimate_bytes(&ga, per, nsp);
     if (r.footprint > s->desc.hbm_budget_bytes)
         return sfail(s, PIC_ENOMEM, "request footprint " + std::to_string(r.footprint) +
                                         " bytes exceeds the server budget");

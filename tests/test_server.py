@@ -119,6 +119,23 @@ def test_admission_by_footprint():
         srv.read_field(c, L.EX, (64, 1, 64))
 
 
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_footprint_estimate_is_the_allocation(order):
+    """The admission estimate equals the bytes the request then allocates, for
+    every serving grid side and a spread of ppc (guards widen with the shape
+    order), so the HBM budget holds for what is actually allocated."""
+    srv = Server(dim=2, shape_order=order, max_active=8, hbm_budget_bytes=1 << 40)
+    rids = []
+    for side, ppc in ((64, 1), (128, 64), (256, 4), (512, 2)):
+        rid = srv.submit((side, 1, side), (32, 1, 32), (0.2, 1, 0.2), 3, plasma=dict(ppc=ppc))
+        rids.append((rid, srv.footprint(rid)))
+    srv.tick()
+    for rid, est in rids:
+        assert srv.poll(rid)["state"] in (L.REQ_ACTIVE, L.REQ_DONE)
+        assert srv.footprint(rid) == est
+    srv.close()
+
+
 def test_langmuir_ripple_oscillates_at_plasma_frequency():
     """Self-checking request: the k = 2 pi / Lx density ripple of a cold plasma
     oscillates at about omega_pe = 1, so Ex reverses sign after half a period."""

@@ -719,9 +719,24 @@ __device__ __forceinline__ bool deposit(const SimDev& S, const JView<typename JA
 // A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
 // deposit<R, DIM, 1, 2>, with fewer instructions.
 template <class R, int DIM>
+__device__ __forceinline__ void deposit_lin_incell_d(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+                                                     R qw, R vy, const R* jf, const Support<1, R>* n,
+                                                     const R* disp);
+
+template <class R, int DIM>
 __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<typename JAcc<R>::type>& V,
                                                    R qw, R vy, const R* jf,
                                                    const Support<1, R>* n, const Support<1, R>* m) {
+    const R disp[3] = {m[0].w[1] - n[0].w[1], m[1].w[1] - n[1].w[1], m[2].w[1] - n[2].w[1]};
+    deposit_lin_incell_d<R, DIM>(S, V, qw, vy, jf, n, disp);
+}
+
+// the same deposit, given the in-cell displacement disp[a] = x^{n+1} - x^n
+// (cells) of each direction
+template <class R, int DIM>
+__device__ __forceinline__ void deposit_lin_incell_d(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+                                                     R qw, R vy, const R* jf, const Support<1, R>* n,
+                                                     const R* disp) {
     using A = Arith<R>;
     const R k12 = A::c(1.0 / 12.0), half = A::c(0.5), one = A::c(1.0);
     const int sy = V.sy, sz = V.sz, lo = S.jlo;
@@ -729,13 +744,13 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<
     JT* Jx = V.base;
     JT* Jy = V.base + V.cs;
     JT* Jz = V.base + 2 * V.cs;
-    const R dx = m[0].w[1] - n[0].w[1], dz = m[2].w[1] - n[2].w[1];
+    const R dx = disp[0], dz = disp[2];
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
     const int bx = n[0].s + lo, bz = n[2].s + lo;
     if constexpr (DIM == 3 && std::is_same<R, dd>::value) {
         // float-float: one loop over the three currents (axis a, transverse b < c)
-        const R dy = m[1].w[1] - n[1].w[1];
+        const R dy = disp[1];
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
         const int by = n[1].s + lo;
@@ -760,7 +775,7 @@ __device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<
         // s = +1 on the diagonal nodes, -1 off it, pf_a = -q w jf_a d_a; with
         // pe_a = pf_a d_b d_c / 12 = -q w jf_a (d_x d_y d_z / 12) and the node
         // weights (1 - m, m) each value is one FMA of pf_a A_b against A_c
-        const R dy = m[1].w[1] - n[1].w[1];
+        const R dy = disp[1];
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
         const int by = n[1].s + lo;
@@ -966,6 +981,183 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     sp.cur[3][p] = A::to(n0);
     sp.cur[4][p] = A::to(n1);
     sp.cur[5][p] = A::to(n2);
+    sp.key[p] = key;
+    warp_hist_add(sp.count, key);
+}
+
+// ---- FP32 variant, linear shapes: positions in 24-bit fixed point --------
+// Adding M = 1.5 * 2^28 to a position X (cells, |X| < 2^27), rounded toward
+// -infinity, truncates it to a multiple of 2^-24 and leaves it, as a
+// fixed-point number with 24 fractional bits, in the low bits of the sum: one
+// FP64 add gives the cell (the bits above 24: floor(X) exactly, negative X
+// too) and the in-cell offset (the low 24) with integer instructions and no
+// branches.  The move is carried in the same units (d rounded to 2^-24 of a
+// cell), so the cell test of x^{n+1}, the in-cell displacement used by the
+// deposit and the stored FP64 position agree exactly; after the first step
+// every stored position lies on the 2^-24 grid.
+constexpr double kFixM = 402653184.0;  // 1.5 * 2^28: ulp 2^-24 over [2^28, 2^29)
+__device__ __forceinline__ long long fix24(double x) {
+    return __double_as_longlong(__dadd_rd(x, kFixM)) - __double_as_longlong(kFixM);
+}
+__device__ __forceinline__ double unfix24(long long b) {
+    return __longlong_as_double(b + __double_as_longlong(kFixM)) - kFixM;  // exact
+}
+__device__ __forceinline__ float frac24(long long b) { return (float)(int)(b & 0xFFFFFFll) * 5.9604644775390625e-8f; }
+
+// double <-> float on the bit patterns without branches: magnitudes below
+// 2^-100 (and zero) become a signed zero (an absolute error below 2^-100,
+// far inside the FP32 variant's tolerance), larger ones round to 24 bits
+__device__ __forceinline__ float f32_of(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long u = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned m = (unsigned)(((u + (1ull << 28)) >> 29) - (896ull << 23));
+    return __uint_as_float(sgn | ((u >> 52) >= 1023 - 100 ? m : 0u));
+}
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+    const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long m = ((unsigned long long)a + (896ull << 23)) << 29;
+    return __longlong_as_double((long long)(sg | (a >= 0x00800000u ? m : 0ull)));
+}
+
+// gather, Boris push and deposit of one particle, FP32 arithmetic, linear shapes
+template <int DIM>
+__device__ __forceinline__ void push_one_f32lin(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
+                                                const float* __restrict__ sEB, const JView<float>& V,
+                                                double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
+                                                const float* jf, const float* dtd, float kq, float qs,
+                                                int64_t p, const PIn& in, int32_t* err) {
+    using A = Arith<float>;
+    const double Xs[3] = {in.X, DIM == 3 ? in.Y : 0.0, in.Z};
+    long long b0[3];
+    int c[3];
+    float f[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (DIM == 2 && a == 1) {
+            b0[a] = 0;
+            c[a] = 0;
+            f[a] = 0.0f;
+            continue;
+        }
+        b0[a] = fix24(Xs[a]);
+        c[a] = (int)(b0[a] >> 24) - tl.o[a];
+        f[a] = frac24(b0[a]);
+        inside = inside && (unsigned)c[a] < (unsigned)S.T[a];
+    }
+    if (!inside) {
+        atomicOr(err, PIC_DERR_BOUNDS);
+        sp.key[p] = S.ntiles;
+        warp_hist_add(sp.count, S.ntiles);
+        return;
+    }
+    // node supports (start c, weight f of the upper node) and half-node ones
+    Support<1, float> nd[3], hf[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (DIM == 2 && a == 1) {
+            nd[1].s = -1;
+            nd[1].w[0] = 1.0f;
+            nd[1].w[1] = 0.0f;
+            hf[1] = nd[1];
+            continue;
+        }
+        nd[a].s = c[a];
+        nd[a].w[1] = f[a];
+        const bool up = f[a] >= 0.5f;
+        if (S.ec) {
+            hf[a].s = c[a];
+            hf[a].w[1] = 0.0f;
+        } else {
+            hf[a].s = up ? c[a] : c[a] - 1;
+            hf[a].w[1] = f[a] + (up ? -0.5f : 0.5f);
+        }
+    }
+    float ev[3], bv[3];
+    gather6<float, 1, DIM>(sEB, P.eb_stride, S.ebs[0], S.ebs[1], nd, hf, ev, bv);
+    const float u0 = f32_of(in.u0), u1 = f32_of(in.u1), u2 = f32_of(in.u2);
+    const float qw = qs * f32_of(in.w);
+
+    // relativistic Boris push
+    const float m0 = fmaf(kq, ev[0], u0), m1 = fmaf(kq, ev[1], u1), m2 = fmaf(kq, ev[2], u2);
+    const float ig = rsqrtf(fmaf(m2, m2, fmaf(m1, m1, fmaf(m0, m0, 1.0f))));
+    const float kg = kq * ig;
+    const float t0 = kg * bv[0], t1 = kg * bv[1], t2 = kg * bv[2];
+    const float sf = 2.0f * __frcp_rn(1.0f + fmaf(t2, t2, fmaf(t1, t1, t0 * t0)));
+    const float s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
+    const float d0 = fmaf(m1, t2, fmaf(-m2, t1, m0));
+    const float d1 = fmaf(m2, t0, fmaf(-m0, t2, m1));
+    const float d2 = fmaf(m0, t1, fmaf(-m1, t0, m2));
+    const float p0 = fmaf(d1, s2, fmaf(-d2, s1, m0));
+    const float p1 = fmaf(d2, s0, fmaf(-d0, s2, m1));
+    const float p2 = fmaf(d0, s1, fmaf(-d1, s0, m2));
+    const float n0 = fmaf(kq, ev[0], p0), n1 = fmaf(kq, ev[1], p1), n2 = fmaf(kq, ev[2], p2);
+    const float ign = rsqrtf(fmaf(n2, n2, fmaf(n1, n1, fmaf(n0, n0, 1.0f))));
+    const float v1 = n1 * ign;
+    const float dv[3] = {(n0 * ign) * dtd[0], DIM == 3 ? v1 * dtd[1] : 0.0f, (n2 * ign) * dtd[2]};
+
+    // x^{n+1} in the same fixed point; in-cell test and displacement
+    long long b1[3];
+    float disp[3];
+    bool same = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (DIM == 2 && a == 1) {
+            b1[a] = 0;
+            disp[a] = 0.0f;
+            continue;
+        }
+        const int di = __float2int_rn(dv[a] * 16777216.0f);
+        b1[a] = b0[a] + di;
+        disp[a] = (float)di * 5.9604644775390625e-8f;
+        same = same && (b1[a] >> 24) == (b0[a] >> 24);
+    }
+    if (same) {
+        deposit_lin_incell_d<float, DIM>(S, V, qw, v1, jf, nd, disp);
+    } else {
+        const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
+        sQw[0 * WQ + slot] = Xs[0];
+        sQw[1 * WQ + slot] = Xs[2];
+        sQw[2 * WQ + slot] = unfix24(b1[0]);
+        sQw[3 * WQ + slot] = unfix24(b1[2]);
+        sQw[4 * WQ + slot] = f64_of(qw);
+        sQw[5 * WQ + slot] = DIM == 3 ? Xs[1] : f64_of(v1);
+        if (DIM == 3) sQw[6 * WQ + slot] = unfix24(b1[1]);
+    }
+
+    // new position, boundary, re-sort key
+    double X = unfix24(b1[0]), Y = DIM == 3 ? unfix24(b1[1]) : 0.0, Z = unfix24(b1[2]);
+    int g[3] = {(int)(b1[0] >> 24), DIM == 3 ? (int)(b1[1] >> 24) : 0, (int)(b1[2] >> 24)};
+    if (g[0] < 0 || g[0] >= S.n[0]) {
+        X = wrap_periodic(X, S.nd[0]);
+        g[0] += g[0] < 0 ? S.n[0] : -S.n[0];
+    }
+    if (DIM == 3 && (g[1] < 0 || g[1] >= S.n[1])) {
+        Y = wrap_periodic(Y, S.nd[1]);
+        g[1] += g[1] < 0 ? S.n[1] : -S.n[1];
+    }
+    int key = -1;
+    if (S.absorb > 0) {
+        if (g[2] < S.absorb || g[2] >= S.n[2] - S.absorb) key = S.ntiles;
+    } else if (g[2] < 0 || g[2] >= S.n[2]) {
+        Z = wrap_periodic(Z, S.nd[2]);
+        g[2] += g[2] < 0 ? S.n[2] : -S.n[2];
+    }
+    if (key < 0) {
+        bool own = (unsigned)(g[0] - tl.o[0]) < (unsigned)S.T[0] && (unsigned)(g[2] - tl.o[2]) < (unsigned)S.T[2];
+        if (DIM == 3) own = own && (unsigned)(g[1] - tl.o[1]) < (unsigned)S.T[1];
+        key = own ? tl.t
+                  : tile_key(S, min(max(g[0], 0), S.n[0] - 1), DIM == 3 ? min(max(g[1], 0), S.n[1] - 1) : 0,
+                             min(max(g[2], 0), S.n[2] - 1));
+    }
+    sp.cur[0][p] = X;
+    if (DIM == 3) sp.cur[1][p] = Y;
+    sp.cur[2][p] = Z;
+    sp.cur[3][p] = f64_of(n0);
+    sp.cur[4][p] = f64_of(n1);
+    sp.cur[5][p] = f64_of(n2);
     sp.key[p] = key;
     warp_hist_add(sp.count, key);
 }
@@ -1283,9 +1475,14 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
 #pragma unroll
                         for (int q = 0; q < PPT; ++q) {
                             const int64_t p = p0 + q * 32 + lane;
-                            if (p < s1)
-                                push_one<R, DIM, ORDER>(S, sp, cur, sEB, sD, V, sQw, s_qtail + warp, P, K.jf, K.dtd,
-                                                        kq, qs, p, in[q], sd->err);
+                            if (p < s1) {
+                                if constexpr (PREC == 2 && ORDER == 1)
+                                    push_one_f32lin<DIM>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq,
+                                                         qs, p, in[q], sd->err);
+                                else
+                                    push_one<R, DIM, ORDER>(S, sp, cur, sEB, sD, V, sQw, s_qtail + warp, P, K.jf,
+                                                            K.dtd, kq, qs, p, in[q], sd->err);
+                            }
                             __syncwarp();
                             const unsigned head = s_qhead[warp], tail = *vtail;
                             if (tail - head >= 32u) {

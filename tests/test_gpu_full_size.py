@@ -78,7 +78,7 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) if b.size else 0.0
 
 
-def check_regions(sim, wl, regions):
+def check_regions(sim, wl, regions, tol=TOL):
     dim = wl["dim"]
     n = wl["ncell"]
     eb = [sim.read_field(c) for c in range(6)]
@@ -123,19 +123,25 @@ def check_regions(sim, wl, regions):
                     sl.append(slice(lo[a] + shrink, hi[a] - shrink))
             sl = tuple(sl)
             worst[f"F{c}"] = rel(after[c][sl], ref.field(c)[sl])
-        bad = {k: v for k, v in worst.items() if not v <= TOL}
-        assert not bad, f"region {lo}-{hi}: parity above {TOL}: {bad}"
+        bad = {k: v for k, v in worst.items() if not v <= tol}
+        assert not bad, f"region {lo}-{hi}: parity above {tol}: {bad}"
         # the region really carried current
         assert np.abs(after[6][sl]).max() > 0
 
 
-@pytest.mark.parametrize("precision", [1, 2], ids=["fp64", "float_float"])
+# FP32 variant: one step of FP32 gather, push and weights (see the derivation
+# beside the parity tests: 3e-5 covers 10 steps; one step sits far inside it)
+TOL_FP32 = 3e-5
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3], ids=["fp64", "float_float", "fp32"])
 def test_foil256_full_size_regions(precision):
     """The bench's workload (256^3 cells, 67.1M particles, laser, damping
     layers): two regions of the foil, one across a box corner."""
     wl = workloads.foil256()
     sim, tuned = bench_state(wl, precision)
-    check_regions(sim, wl, [((100, 100, 122), (124, 124, 142)), ((20, 150, 120), (44, 174, 144))])
+    check_regions(sim, wl, [((100, 100, 122), (124, 124, 142)), ((20, 150, 120), (44, 174, 144))],
+                  tol=TOL if precision != 3 else TOL_FP32)
     sim.close()
 
 

@@ -552,13 +552,14 @@ def test_energy_conserving_gather_suppresses_grid_heating():
     assert abs(drift[True]) < 1e-3, drift
 
 
-@pytest.mark.parametrize("precision", [1, 2], ids=["fp64", "float_float"])
+@pytest.mark.parametrize("precision", [1, 2, 3], ids=["fp64", "float_float", "fp32"])
 @pytest.mark.parametrize("order", [1, 2, 3])
 def test_degenerate_positions_and_momenta(order, precision):
     """Particles exactly on nodes and half nodes, at 0 and just below the
-    domain length (the integer floor paths, the periodic wrap), with momenta 0,
+    domain length (the integer floor paths, the periodic wrap; the FP32
+    variant's fixed-point cell must stay the exact floor), with momenta 0,
     +-1e-300 (below the float range: the float-float conversions' FP64
-    route) and +-1e3 (gamma ~ 1e3), in random fields."""
+    route, a flush to zero in FP32) and +-1e3 (gamma ~ 1e3), in random fields."""
     n, box, dx = (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3)
     rng = np.random.default_rng(500 + order)
     L = np.array(n) * np.array(dx)
@@ -585,11 +586,11 @@ def test_degenerate_positions_and_momenta(order, precision):
           "dt": 0.99 * dx[0] / np.sqrt(3.0), "order": order, "absorb": 0, "species": [sp], "rho0": 0.0}
     fields = workloads.random_fields(12, n, amp=0.2)
     sim, ref = make_gpu(wl, fields), make_oracle(wl, fields)
-    if precision == 2:
-        sim.set_launch(precision=2)
+    if precision != 1:
+        sim.set_launch(precision=precision)
     sim.step(3)
     ref.step(3)
-    compare(sim, ref, wl)
+    compare(sim, ref, wl, tol=TOL if precision != 3 else TOL_FP32)
 
 
 # FP32 variant: every gather, Boris and deposit-weight operation rounds to 2^-24

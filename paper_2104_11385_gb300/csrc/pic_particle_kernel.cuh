@@ -425,8 +425,9 @@ __device__ __forceinline__ void tile_origin(const SimDev& S, int t, int o[3]) {
 
 __device__ __forceinline__ int modi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
-// tile key of a global cell (box-major numbering)
-__device__ __forceinline__ int tile_key(const SimDev& S, int ix, int iy, int iz) {
+// tile key of a global cell (box-major numbering); SV: SimDev or HotSim
+template <class SV>
+__device__ __forceinline__ int tile_key(const SV& S, int ix, int iy, int iz) {
     int bx = ix / S.bsz[0], by = iy / S.bsz[1], bz = iz / S.bsz[2];
     int tx = (ix - bx * S.bsz[0]) / S.T[0];
     int ty = (iy - by * S.bsz[1]) / S.T[1];
@@ -440,6 +441,44 @@ __device__ __forceinline__ void warp_hist_add(int32_t* count, int key) {
     unsigned peers = __match_any_sync(act, key);
     int lane = threadIdx.x & 31;
     if (lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+}
+
+// The fields of a simulation and of its species that the particle loop reads,
+// staged in shared memory once per work unit.  Read from the SimDev in global
+// memory they would be fetched again for every particle (the loop's stores to
+// the particle arrays might alias them as far as the compiler can tell).
+struct HotSp {
+    double* cur[7];
+    int32_t* key;
+    int32_t* count;
+};
+struct HotSim {
+    double nd[3];
+    int T[3], n[3], bsz[3], nb[3], tpb[3], ebs[3];
+    int tiles_per_box, ntiles, absorb, ec, jlo;
+    HotSp sp[PIC_MAXSP];
+};
+
+__device__ __forceinline__ void stage_hot(HotSim& h, const SimDev& S) {
+    for (int a = 0; a < 3; ++a) {
+        h.nd[a] = S.nd[a];
+        h.T[a] = S.T[a];
+        h.n[a] = S.n[a];
+        h.bsz[a] = S.bsz[a];
+        h.nb[a] = S.nb[a];
+        h.tpb[a] = S.tpb[a];
+        h.ebs[a] = S.ebs[a];
+    }
+    h.tiles_per_box = S.tiles_per_box;
+    h.ntiles = S.ntiles;
+    h.absorb = S.absorb;
+    h.ec = S.ec;
+    h.jlo = S.jlo;
+    for (int i = 0; i < S.nsp; ++i) {
+        for (int a = 0; a < 7; ++a) h.sp[i].cur[a] = S.sp[i].cur[a];
+        h.sp[i].key = S.sp[i].key;
+        h.sp[i].count = S.sp[i].count;
+    }
 }
 
 // Shared-memory layout: six E/B tiles (TMA destinations), three J tiles, and
@@ -549,8 +588,8 @@ struct JView {
 // Prefix sums of DS along each current's own direction times the transverse
 // weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3 = A_a A_b + DS_a DS_b / 12
 // with A = S0 + DS/2.  qw and vy in R; the prefactors -1/(dA dt) come from jf.
-template <class R, int DIM, int ORDER, int W>
-__device__ __forceinline__ bool deposit(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+template <class R, int DIM, int ORDER, int W, class SV>
+__device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R>::type>& V,
                                         R qw, R vy, const R* jf, const Support<ORDER, R>& n0,
                                         const Support<ORDER, R>& n1, const Support<ORDER, R>& n2,
                                         const Support<ORDER, R>& m0, const Support<ORDER, R>& m1,
@@ -718,23 +757,23 @@ __device__ __forceinline__ bool deposit(const SimDev& S, const JView<typename JA
 // has one term and the transverse weight A_a A_b + DS_a DS_b / 12 is
 // A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
 // deposit<R, DIM, 1, 2>, with fewer instructions.
-template <class R, int DIM>
-__device__ __forceinline__ void deposit_lin_incell_d(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+template <class R, int DIM, class SV>
+__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<typename JAcc<R>::type>& V,
                                                      R qw, R vy, const R* jf, const Support<1, R>* n,
                                                      const R* disp);
 
-template <class R, int DIM>
-__device__ __forceinline__ void deposit_lin_incell(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+template <class R, int DIM, class SV>
+__device__ __forceinline__ void deposit_lin_incell(const SV& S, const JView<typename JAcc<R>::type>& V,
                                                    R qw, R vy, const R* jf,
                                                    const Support<1, R>* n, const Support<1, R>* m) {
     const R disp[3] = {m[0].w[1] - n[0].w[1], m[1].w[1] - n[1].w[1], m[2].w[1] - n[2].w[1]};
-    deposit_lin_incell_d<R, DIM>(S, V, qw, vy, jf, n, disp);
+    deposit_lin_incell_d<R, DIM, SV>(S, V, qw, vy, jf, n, disp);
 }
 
 // the same deposit, given the in-cell displacement disp[a] = x^{n+1} - x^n
 // (cells) of each direction
-template <class R, int DIM>
-__device__ __forceinline__ void deposit_lin_incell_d(const SimDev& S, const JView<typename JAcc<R>::type>& V,
+template <class R, int DIM, class SV>
+__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<typename JAcc<R>::type>& V,
                                                      R qw, R vy, const R* jf, const Support<1, R>* n,
                                                      const R* disp) {
     using A = Arith<R>;
@@ -842,8 +881,8 @@ struct PIn {
     double X, Y, Z, u0, u1, u2, w;
 };
 
-template <int DIM>
-__device__ __forceinline__ PIn load_one(const SpeciesDev& sp, int64_t p) {
+template <int DIM, class SPV>
+__device__ __forceinline__ PIn load_one(const SPV& sp, int64_t p) {
     PIn in;
     in.X = sp.cur[0][p];
     in.Y = (DIM == 3) ? sp.cur[1][p] : 0.0;
@@ -858,8 +897,8 @@ __device__ __forceinline__ PIn load_one(const SpeciesDev& sp, int64_t p) {
 // Gather, Boris push, and deposit of one particle.  Particles that keep their
 // support in every direction deposit at once on the small window; the others
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
-template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
+template <class R, int DIM, int ORDER, class SV, class SPV>
+__device__ __forceinline__ void push_one(const SV& S, const SPV& sp, const Tile& tl,
                                          const R* __restrict__ sEB, const R* __restrict__ sD,
                                          const JView<typename JAcc<R>::type>& V,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
@@ -934,7 +973,7 @@ __device__ __forceinline__ void push_one(const SimDev& S, const SpeciesDev& sp, 
     bool same = mv[0].s == nd[0].s && mv[2].s == nd[2].s && (DIM == 2 || mv[1].s == nd[1].s);
     if (same) {
         if constexpr (ORDER == 1)
-            deposit_lin_incell<R, DIM>(S, V, qw, v1, jf, nd, mv);
+            deposit_lin_incell<R, DIM, SV>(S, V, qw, v1, jf, nd, mv);
         else
             deposit<R, DIM, ORDER, ORDER + 1>(S, V, qw, v1, jf, nd[0], nd[1], nd[2], mv[0], mv[1], mv[2]);
     } else {
@@ -1022,8 +1061,8 @@ __device__ __forceinline__ double f64_of(float f) {
 }
 
 // gather, Boris push and deposit of one particle, FP32 arithmetic, linear shapes
-template <int DIM>
-__device__ __forceinline__ void push_one_f32lin(const SimDev& S, const SpeciesDev& sp, const Tile& tl,
+template <int DIM, class SV, class SPV>
+__device__ __forceinline__ void push_one_f32lin(const SV& S, const SPV& sp, const Tile& tl,
                                                 const float* __restrict__ sEB, const JView<float>& V,
                                                 double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                                 const float* jf, const float* dtd, float kq, float qs,
@@ -1115,7 +1154,7 @@ __device__ __forceinline__ void push_one_f32lin(const SimDev& S, const SpeciesDe
         same = same && (b1[a] >> 24) == (b0[a] >> 24);
     }
     if (same) {
-        deposit_lin_incell_d<float, DIM>(S, V, qw, v1, jf, nd, disp);
+        deposit_lin_incell_d<float, DIM, SV>(S, V, qw, v1, jf, nd, disp);
     } else {
         const unsigned slot = atomicAdd(s_tail, 1u) & (WQ - 1);
         sQw[0 * WQ + slot] = Xs[0];
@@ -1282,6 +1321,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     double* smem = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     __shared__ int s_unit, s_list, s_abort;
+    __shared__ HotSim s_hot;
     __shared__ unsigned s_qhead[QMAXWARPS], s_qtail[QMAXWARPS];
     __shared__ unsigned long long s_cost;
 
@@ -1337,6 +1377,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 ++visited;
             }
             s_unit = u;
+            // every warp has left the previous unit (its closing barrier): restage
+            if (u >= 0) stage_hot(s_hot, sims[sd->units[u].sim]);
         }
         __syncthreads();
         const int u = s_unit;
@@ -1470,18 +1512,18 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
 #pragma unroll
                         for (int q = 0; q < PPT; ++q) {
                             const int64_t p = p0 + q * 32 + lane;
-                            if (p < s1) in[q] = load_one<DIM>(sp, p);
+                            if (p < s1) in[q] = load_one<DIM>(s_hot.sp[spi], p);
                         }
 #pragma unroll
                         for (int q = 0; q < PPT; ++q) {
                             const int64_t p = p0 + q * 32 + lane;
                             if (p < s1) {
                                 if constexpr (PREC == 2 && ORDER == 1)
-                                    push_one_f32lin<DIM>(S, sp, cur, sEB, V, sQw, s_qtail + warp, P, K.jf, K.dtd, kq,
-                                                         qs, p, in[q], sd->err);
+                                    push_one_f32lin<DIM>(s_hot, s_hot.sp[spi], cur, sEB, V, sQw, s_qtail + warp, P,
+                                                         K.jf, K.dtd, kq, qs, p, in[q], sd->err);
                                 else
-                                    push_one<R, DIM, ORDER>(S, sp, cur, sEB, sD, V, sQw, s_qtail + warp, P, K.jf,
-                                                            K.dtd, kq, qs, p, in[q], sd->err);
+                                    push_one<R, DIM, ORDER>(s_hot, s_hot.sp[spi], cur, sEB, sD, V, sQw, s_qtail + warp,
+                                                            P, K.jf, K.dtd, kq, qs, p, in[q], sd->err);
                             }
                             __syncwarp();
                             const unsigned head = s_qhead[warp], tail = *vtail;

@@ -507,14 +507,17 @@ struct SmemPlan {
 // jshared: the J tile lives in shared memory (FP32 variant); otherwise the
 // current goes to global memory and the J region is empty.  xdiff: the x
 // differences of the staged E/B tile are kept beside it (linear FP64).
-// Layout: E/B tile | x differences | J tile | (FP32 variant) rings.
-__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared, bool xdiff = false) {
+// fcopy: the second region holds the E/B tile converted to floats, with the
+// same component stride in floats (FP32 variant).
+// Layout: E/B tile (TMA) | x differences or float copy | J tile.
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared, bool xdiff = false,
+                                              bool fcopy = false) {
     SmemPlan p;
     p.eb_vol = ebs[0] * ebs[1] * ebs[2];
     p.d_vol = xdiff ? (ebs[0] - 1) * ebs[1] * ebs[2] : 0;
     p.j_vol = jshared ? js[0] * js[1] * js[2] : 0;
     p.eb_stride = (p.eb_vol + 15) & ~15;
-    p.d_stride = (p.d_vol + 15) & ~15;
+    p.d_stride = fcopy ? ((p.eb_stride / 2 + 15) & ~15) : ((p.d_vol + 15) & ~15);
     p.j_stride = (p.j_vol + 1) & ~1;
     p.bytes = (size_t)(6 * p.eb_stride + 6 * p.d_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
     return p;
@@ -1315,6 +1318,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     using JT = typename JAcc<R>::type;
     constexpr bool GJ = JAcc<R>::global;
     constexpr bool XD = PREC == 0 && ORDER == 1;  // x-difference tile beside the E/B tile
+    constexpr bool FC = PREC == 2;                // float copy of the E/B tile beside it
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -1342,9 +1346,9 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     cur.t = -1;
     int visited = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ring of cell-crossing particles: global scratch with the global J
-    // target (FP64, float-float), shared memory after the J tile otherwise
-    double* const gring = GJ ? sd->rings + ((size_t)blockIdx.x * QMAXWARPS + warp) * PIC_RING_DOUBLES : nullptr;
+    // ring of cell-crossing particles, in global scratch (L1/L2 resident; a
+    // drain runs once per 32 crossings)
+    double* const gring = sd->rings + ((size_t)blockIdx.x * QMAXWARPS + warp) * PIC_RING_DOUBLES;
 
     // global J target: a warp's ring of cell-crossing particles outlives tile
     // changes; it is drained when the simulation changes (rings hold one
@@ -1353,7 +1357,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         if constexpr (GJ) {
             const unsigned head = s_qhead[warp], tail = s_qtail[warp];
             if (tail != head) {
-                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false, XD);
+                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false, XD, FC);
                 const SimConsts<R, DIM> K(CS);
                 drain<R, DIM, ORDER>(CS, cur, j_view<JT>(CS, cur, nullptr, CP), gring, head, tail - head, K.jf,
                                      sd->err);
@@ -1387,11 +1391,11 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         const SimDev& S = sims[unit.sim];
         const bool cap_clk = (S.capture & 1) != 0, cap_time = (S.capture & 2) != 0;
         const uint64_t t_unit0 = (threadIdx.x == 0 && cap_time) ? globaltimer() : 0ull;
-        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ, XD);
+        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ, XD, FC);
         double* sEBd = smem;
-        const R* sEB = reinterpret_cast<const R*>(smem);
-        double* sDd = smem + 6 * P.eb_stride;   // x differences (linear FP64)
-        double* sJd = sDd + 6 * P.d_stride;     // J tile (FP32 variant only); its rings follow it
+        double* sDd = smem + 6 * P.eb_stride;   // x differences (linear FP64), float copy (FP32)
+        const R* sEB = reinterpret_cast<const R*>(FC ? sDd : smem);
+        double* sJd = sDd + 6 * P.d_stride;     // J tile (FP32 variant only)
         JT* sJ = reinterpret_cast<JT*>(sJd);
         unsigned long long my_clk = 0ull;
         const SimConsts<R, DIM> K(S);
@@ -1415,7 +1419,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                     if constexpr (!GJ) {
                         if (cur.t >= 0) {
                             const SimDev& CS = sims[cur.sim];
-                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD);
+                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD, FC);
                             flush_j<DIM, ORDER>(CS, cur,
                                                 reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
                             __syncthreads();
@@ -1476,35 +1480,18 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         __syncthreads();
                     }
                     if constexpr (PREC == 2) {
-                        // E/B tile to FP32, compacted in place: float i lands on
-                        // bytes of double i/2 <= i, so each round reads its 4 x
-                        // blockDim doubles before any of its floats is written
-                        // (a round's floats cover doubles below its own end)
-                        float* sEBf = reinterpret_cast<float*>(sEBd);
+                        // E/B tile to FP32 in the float-copy region, one pass
+                        float* sEBf = reinterpret_cast<float*>(sDd);
                         const int ntot = 6 * P.eb_stride;
-                        constexpr int KR = 4;
-                        for (int base = 0; base < ntot; base += KR * blockDim.x) {
-                            double v[KR];
-#pragma unroll
-                            for (int q = 0; q < KR; ++q) {
-                                const int i = base + q * blockDim.x + threadIdx.x;
-                                v[q] = i < ntot ? sEBd[i] : 0.0;
-                            }
-                            __syncthreads();
-#pragma unroll
-                            for (int q = 0; q < KR; ++q) {
-                                const int i = base + q * blockDim.x + threadIdx.x;
-                                if (i < ntot) sEBf[i] = f32_from(v[q]);
-                            }
-                            __syncthreads();
-                        }
+                        for (int i = threadIdx.x; i < ntot; i += blockDim.x) sEBf[i] = f32_of(sEBd[i]);
+                        __syncthreads();
                     }
                 }
                 const unsigned long long c0 = cap_clk ? clock64() : 0ull;
                 {
                     // per-warp loop: no CTA barrier until the tile changes
                     const JView<JT> V = j_view<JT>(S, cur, sJ, P);
-                    double* sQw = GJ ? gring : sJd + 3 * P.j_stride + warp * (QFields<DIM>::n * WQ);
+                    double* sQw = gring;
                     const R* sD = XD ? reinterpret_cast<const R*>(sDd) : nullptr;
                     volatile unsigned* vtail = s_qtail + warp;
                     for (int64_t p0 = s0 + warp * (32 * PPT); p0 < s1; p0 += (int64_t)blockDim.x * PPT) {
@@ -1571,7 +1558,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         } else {
             __syncthreads();
             const SimDev& CS = sims[cur.sim];
-            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD);
+            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD, FC);
             flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
         }
     }

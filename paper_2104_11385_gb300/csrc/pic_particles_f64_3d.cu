@@ -13,10 +13,8 @@ size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, 
         js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
     }
     if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
-    // tiles (the x differences for linear FP64, the J tile and one crossing
-    // ring per warp for the FP32 variant, prec 2; the other variants keep
-    // their rings in global memory) + alignment slack of the dynamic base
-    const int qf = dim == 3 ? QFields<3>::n : QFields<2>::n;
-    const size_t rings = prec == 2 ? (size_t)(threads / 32) * qf * WQ * sizeof(double) : 0;
-    return smem_plan(ebs, js, prec == 2, uses_xdiff(prec, order)).bytes + rings + 128;
+    // tiles (the x differences for linear FP64; the float copy of the E/B
+    // tile and the J tile for the FP32 variant, prec 2) + alignment slack of
+    // the dynamic base; the rings of crossing particles are in global memory
+    return smem_plan(ebs, js, prec == 2, uses_xdiff(prec, order), prec == 2).bytes + 128;
 }

@@ -130,6 +130,10 @@ def parse():
     ap.add_argument("--timeline", type=int, default=0,
                     help="instead of the bench line: N steps of the workload under each load-balancing mode "
                          "(none / static / dynamic), with E and the time per step every interval")
+    ap.add_argument("--timeline-modes", default="none,static,dynamic,dynamic_sfc",
+                    help="comma-separated modes of --timeline: none, static, dynamic (knapsack, device-clock "
+                         "costs), dynamic_sfc, dynamic_heuristic (knapsack, particle/cell-count costs), "
+                         "dynamic_kernel_time")
     return ap.parse_args()
 
 
@@ -738,13 +742,18 @@ def run_timeline(args):
     sched = pic.SCHED_LISTS if args.sched == "lists" else pic.SCHED_QUEUE
     stream = torch.cuda.Stream()
     out = {}
-    for name, mode, policy in (("none", pic.LB_NONE, pic.POLICY_KNAPSACK),
-                               ("static", pic.LB_STATIC, pic.POLICY_KNAPSACK),
-                               ("dynamic", pic.LB_DYNAMIC, pic.POLICY_KNAPSACK),
-                               ("dynamic_sfc", pic.LB_DYNAMIC, pic.POLICY_SFC)):
+    known = {"none": (pic.LB_NONE, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
+             "static": (pic.LB_STATIC, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
+             "dynamic": (pic.LB_DYNAMIC, pic.POLICY_KNAPSACK, pic.COST_DEVICE_CLOCK),
+             "dynamic_sfc": (pic.LB_DYNAMIC, pic.POLICY_SFC, pic.COST_DEVICE_CLOCK),
+             "dynamic_heuristic": (pic.LB_DYNAMIC, pic.POLICY_KNAPSACK, pic.COST_HEURISTIC),
+             "dynamic_kernel_time": (pic.LB_DYNAMIC, pic.POLICY_KNAPSACK, pic.COST_KERNEL_TIME)}
+    modes = [m for m in args.timeline_modes.split(",") if m]
+    for name in modes:
+        mode, policy, cost = known[name]
         sim = pic.from_workload(wl, stream=stream.cuda_stream)
         sim.set_lb_params(mode=mode, interval=interval, theta=0.10, policy=policy,
-                          cost=pic.COST_DEVICE_CLOCK, split=args.split, sched=sched)
+                          cost=cost, split=args.split, sched=sched)
         sim.set_launch(threads=args.threads or 256, ctas_per_sm=args.ctas_per_sm or 2,
                        precision=args.precision)
         ms, eff = [], []
@@ -761,6 +770,8 @@ def run_timeline(args):
             # E of the mapping used during this interval: the load-balancing
             # call at its end measured it (e_old); otherwise read it and start
             # a new cost window
+            # (for dynamic_heuristic and dynamic_kernel_time that call's E is in
+            # its own cost measure; the time per step is the common yardstick)
             eff.append(log[-1]["e_old"] if log else sim.efficiency(reset_window=True))
         lbl = sim.lb_log()
         sim.close()
@@ -773,11 +784,14 @@ def run_timeline(args):
             "interval": interval, "sched": args.sched, "theta": 0.10,
             "launch": {"threads": args.threads or 256, "ctas_per_sm": args.ctas_per_sm or 2,
                        "precision": args.precision},
-            "speedup_static_over_none": out["none"]["total_ms"] / out["static"]["total_ms"],
-            "speedup_dynamic_over_none": out["none"]["total_ms"] / out["dynamic"]["total_ms"],
-            "speedup_dynamic_over_static": out["static"]["total_ms"] / out["dynamic"]["total_ms"],
-            "speedup_knapsack_over_sfc": out["dynamic_sfc"]["total_ms"] / out["dynamic"]["total_ms"],
             "modes": out}
+    for a, b, key in (("none", "static", "speedup_static_over_none"), ("none", "dynamic", "speedup_dynamic_over_none"),
+                      ("static", "dynamic", "speedup_dynamic_over_static"),
+                      ("dynamic_sfc", "dynamic", "speedup_knapsack_over_sfc"),
+                      ("dynamic_heuristic", "dynamic", "speedup_device_clock_over_heuristic"),
+                      ("dynamic_kernel_time", "dynamic", "speedup_device_clock_over_kernel_time")):
+        if a in out and b in out:
+            line[key] = out[a]["total_ms"] / out[b]["total_ms"]
     print(json.dumps(line, default=_jsonable), flush=True)
 
 

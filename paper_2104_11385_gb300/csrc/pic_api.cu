@@ -498,6 +498,16 @@ pic_status configure_launch(pic_sim* s) {
     return PIC_OK;
 }
 
+// block sums of the multi-block histogram scan, enough for the tile count
+pic_status ensure_scan_part(pic_sim* s) {
+    SimDev& h = s->h;
+    const int64_t need = ((int64_t)h.ntiles + 1 + 1023) / 1024;
+    if (need <= h.scan_part_cap) return PIC_OK;
+    TRY(dalloc(s, &h.scan_part, (size_t)need));
+    h.scan_part_cap = need;
+    return PIC_OK;
+}
+
 // Re-tiles the simulation with tile edge t in every active direction: tile
 // maps for the new staged tile, sort arrays for the new tile count, and every
 // species re-sorted by the new tiles.  Units (box chunks) are unaffected.
@@ -534,6 +544,7 @@ pic_status retile(pic_sim* s, int t) {
             TRY(dalloc(s, &sp.off, h.ntiles + 2));
             s->tiles_cap[i] = h.ntiles;
         }
+        TRY(ensure_scan_part(s));
         CU(s, cudaMemsetAsync(sp.count, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
         CU(s, cudaMemsetAsync(sp.cursor, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
         CU(s, cudaMemsetAsync(sp.off, 0, (h.ntiles + 2) * sizeof(int64_t), s->stream));
@@ -652,6 +663,7 @@ int64_t pic_internal_estimate_bytes(const pic_grid_desc* g, const int64_t* np, i
     auto r = [](int64_t n, int64_t sz) { return std::max<int64_t>(n, 1) * sz; };
     int64_t b = r(pvol * PIC_NCOMP, 8) + 2 * r(nboxes, 8) + 8 + 4 + (int64_t)sizeof(SimDev) + (int64_t)pic_ring_bytes(pic_sm_count()) +
                 (int64_t)sizeof(SchedDev) + r(8193, 4) + r(8192, 4) + r(2, 4) + r(4, 8) + r(nboxes, 8);
+    if (nsp > 0) b += r((ntiles + 1 + 1023) / 1024, 8);  // block sums of the histogram scan
     for (int i = 0; i < nsp; ++i) {
         const int64_t cap = std::max<int64_t>(np[i], 1);
         b += 14 * r(cap, 8) + 2 * r(cap, 8) + r(cap, 4) + 2 * r(ntiles + 1, 4) + r(ntiles + 2, 8) + 8;
@@ -847,6 +859,7 @@ pic_status pic_add_species(pic_sim* s, double charge, double mass, int64_t np,
     TRY(dalloc(s, &sp.cursor, h.ntiles + 1));
     TRY(dalloc(s, &sp.off, h.ntiles + 2));
     s->tiles_cap[idx] = h.ntiles;
+    TRY(ensure_scan_part(s));
     TRY(dalloc(s, &sp.np_prev, 1));
     CU(s, cudaMemsetAsync(sp.count, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));
     CU(s, cudaMemsetAsync(sp.cursor, 0, (h.ntiles + 1) * sizeof(int32_t), s->stream));

@@ -87,6 +87,8 @@ struct SimDev {
     uint64_t* cost_time;  // [nboxes] summed %globaltimer ns of the box's units (kernel-time cost)
     int64_t* step;        // device step counter
     int32_t* err;         // device error word (shared with the schedule)
+    int64_t* scan_part;   // [scan_part_cap] block sums of the multi-block histogram scan
+    int64_t scan_part_cap;
     const int32_t* owner; // box sharding: rank owning each box (nullptr: every box is this rank's)
     int rank;             // this simulation's rank when sharded
     LaserDev las;

@@ -69,6 +69,81 @@ __global__ void __launch_bounds__(1024) pic_scan_kernel(SimDev* __restrict__ sim
     if (threadIdx.x == 0) *sp.np_prev = s_np_prev;
 }
 
+// The same scan for large tile counts, in three launches over blocks of 1024
+// entries: block sums; their exclusive scan in one block (which also records
+// the kept count of the buffer just pushed and the total); then each block's
+// own exclusive scan plus its offset, clearing count and cursor.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+    __shared__ int64_t s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int64_t before = warp > 0 ? s_warp[warp - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pic_scan_part_kernel(SimDev* __restrict__ sims, int sp_idx) {
+    SimDev& S = sims[0];
+    SpeciesDev& sp = S.sp[sp_idx];
+    const int N = S.ntiles + 1;
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    int64_t total;
+    block_exclusive_scan(i < N ? (int64_t)sp.count[i] : 0, &total);
+    if (threadIdx.x == 0) S.scan_part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pic_scan_top_kernel(SimDev* __restrict__ sims, int sp_idx, int nparts) {
+    SimDev& S = sims[0];
+    SpeciesDev& sp = S.sp[sp_idx];
+    const int per = (nparts + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per, i1 = min(nparts, i0 + per);
+    int64_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += S.scan_part[i];
+    int64_t total;
+    int64_t run = block_exclusive_scan(sum, &total);
+    if (threadIdx.x == 0) *sp.np_prev = sp.off[S.ntiles];  // kept count of the buffer just pushed
+    for (int i = i0; i < i1; ++i) {
+        const int64_t c = S.scan_part[i];
+        S.scan_part[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) sp.off[S.ntiles + 1] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pic_scan_final_kernel(SimDev* __restrict__ sims, int sp_idx) {
+    SimDev& S = sims[0];
+    SpeciesDev& sp = S.sp[sp_idx];
+    const int N = S.ntiles + 1;
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int64_t c = i < N ? (int64_t)sp.count[i] : 0;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan(c, &total);
+    if (i < N) {
+        sp.off[i] = S.scan_part[blockIdx.x] + ex;
+        sp.count[i] = 0;
+        sp.cursor[i] = 0;
+    }
+}
+
 template <int DIM>
 __global__ void pic_scatter_kernel(SimDev* __restrict__ sims, const int* __restrict__ slots, int sp_idx) {
     const SimDev& S = sims[slots ? slots[blockIdx.y] : 0];
@@ -252,7 +327,15 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t pic_launch_sort(const SimDev* dsim, const SimDev& hsim, int sp, cudaStream_t st) {
     SimDev* d = const_cast<SimDev*>(dsim);
-    pic_scan_kernel<<<1, 1024, 0, st>>>(d, nullptr, sp);
+    const int64_t N = (int64_t)hsim.ntiles + 1;
+    const int64_t nparts = (N + kScanBlock - 1) / kScanBlock;
+    if (N > 8 * kScanBlock && hsim.scan_part && nparts <= hsim.scan_part_cap) {
+        pic_scan_part_kernel<<<(int)nparts, kScanBlock, 0, st>>>(d, sp);
+        pic_scan_top_kernel<<<1, kScanBlock, 0, st>>>(d, sp, (int)nparts);
+        pic_scan_final_kernel<<<(int)nparts, kScanBlock, 0, st>>>(d, sp);
+    } else {
+        pic_scan_kernel<<<1, 1024, 0, st>>>(d, nullptr, sp);
+    }
     int64_t cap = hsim.sp[sp].cap;
     if (hsim.dim == 3) pic_scatter_kernel<3><<<grid_for(cap, 256), 256, 0, st>>>(d, nullptr, sp);
     else pic_scatter_kernel<2><<<grid_for(cap, 256), 256, 0, st>>>(d, nullptr, sp);

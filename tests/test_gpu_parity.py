@@ -242,6 +242,19 @@ def test_tile_size_and_particles_per_thread_do_not_change_physics(case, precisio
     compare(sim, ref, wl)
 
 
+def test_many_tiles_multi_block_scan():
+    """16384 tiles (128 x 128 x 64 cells, 4^3 tiles): the per-tile histogram is
+    scanned by the multi-block path; particles, currents and fields stay on the
+    oracle's trajectory."""
+    n, box = (128, 128, 64), (8, 8, 8)
+    wl = workloads.random_plasma(420, 3, n, box, (0.3, 0.3, 0.3), 1, nspecies=2, npart=20000, umax=1.5)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    sim.set_launch(tile=4)
+    sim.step(4)
+    ref.step(4)
+    compare(sim, ref, wl)
+
+
 def test_retile_between_steps():
     """A tile change after some steps re-sorts every species; the run stays on
     the oracle's trajectory, and bad tile sizes are refused."""

@@ -49,18 +49,18 @@ BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 
 # DRAM traffic of the FP64 particle kernel <3,1> from one ncu capture on the
 # foil recipe at half extents (128^3 cells, 8,388,608 particles; 256 threads,
-# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 506.90 + 413.93 MB
+# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 501.95 + 409.69 MB
 # (the capture's summary sits with the ncu profiles).  Traffic grows with the
 # particle count, so a full launch is scaled by particles.  The figure is
 # reported only while the kernel's code (comments aside) hashes to what was
 # captured.
-TRAFFIC_CAPTURE = {"bytes_per_particle": (506.900992e6 + 413.934592e6) / 8388608, "dim": 3, "order": 1,
+TRAFFIC_CAPTURE = {"bytes_per_particle": (501.952256e6 + 409.693184e6) / 8388608, "dim": 3, "order": 1,
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
                                "paper_2104_11385_gb300/csrc/pic_particles_f64_3d.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h",
                                "paper_2104_11385_gb300/csrc/pic_sync.cuh"),
-                   "sha256": "14b5ee736e3624b76dfce49b1272b60221199e71ddf603557549f7c33cbdb344"}
+                   "sha256": "236b1369cd5c9070d0c8776870260598d5d5a2e5ef2201316e15340a4a13a5d2"}
 
 
 def _kernel_sources_sha(paths):

@@ -49,18 +49,18 @@ BYTES_PER_CELL = 120.0      # read E,B,J (72) + write E,B (48)
 
 # DRAM traffic of the FP64 particle kernel <3,1> from one ncu capture on the
 # foil recipe at half extents (128^3 cells, 8,388,608 particles; 256 threads,
-# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 501.95 + 409.69 MB
+# 2 CTAs/SM): dram__bytes_read.sum + dram__bytes_write.sum = 501.01 + 409.76 MB
 # (the capture's summary sits with the ncu profiles).  Traffic grows with the
 # particle count, so a full launch is scaled by particles.  The figure is
 # reported only while the kernel's code (comments aside) hashes to what was
 # captured.
-TRAFFIC_CAPTURE = {"bytes_per_particle": (501.952256e6 + 409.693184e6) / 8388608, "dim": 3, "order": 1,
+TRAFFIC_CAPTURE = {"bytes_per_particle": (501.010432e6 + 409.757440e6) / 8388608, "dim": 3, "order": 1,
                    "sources": ("paper_2104_11385_gb300/csrc/pic_particle_kernel.cuh",
                                "paper_2104_11385_gb300/csrc/pic_particles_f64_3d.cu",
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h",
                                "paper_2104_11385_gb300/csrc/pic_sync.cuh"),
-                   "sha256": "236b1369cd5c9070d0c8776870260598d5d5a2e5ef2201316e15340a4a13a5d2"}
+                   "sha256": "b7be8a1a47e4129732e72148b93f3b15890e5eec9a8e4e277e1e2d2d6e4fff71"}
 
 
 def _kernel_sources_sha(paths):
@@ -115,6 +115,8 @@ def parse():
                     help="particle push arithmetic of the main arm: 1 FP64, 2 float-float, 3 FP32")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0, help="cells per tile edge with --threads (0: library default)")
+    ap.add_argument("--ppt", type=int, default=0, help="particles per thread with --threads (0: library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--no-cost-arms", action="store_true")
@@ -306,7 +308,7 @@ def run_ours(args, rank, world, wl=None, full=True):
     sim.set_lb_params(**lbkw)
     sim.set_launch(precision=args.precision)
     if args.threads or args.ctas_per_sm:
-        sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+        sim.set_launch(threads=args.threads, ctas_per_sm=args.ctas_per_sm, tile=args.tile, ppt=args.ppt)
         tuned = sim.get_launch()
     else:
         tuned = sim.autotune(steps_per_candidate=2)  # threads, CTAs/SM, units per worker
@@ -323,7 +325,7 @@ def run_ours(args, rank, world, wl=None, full=True):
     release(sim)
     tkw = {k: tuned[k] for k in ("threads", "ctas_per_sm", "split", "tile", "ppt")}
 
-    # ---- reduced-precision variants (float-float push; FP32 push with FP32 tile sums)
+    # ---- reduced-precision variants (float-float push; FP32 push)
     variants = {}
     if not args.no_mixed and args.precision == 1:
         for prec in (2, 3):
@@ -346,9 +348,9 @@ def run_ours(args, rank, world, wl=None, full=True):
         variants[2]["arithmetic"] = ("float-float (FP32 pairs, ~48-bit significand) gather, Boris and deposit "
                                      "weights; FP64 storage, positions and current sums; parity 1e-10 vs the "
                                      "FP64 oracle (tests/test_gpu_parity.py)")
-        variants[3]["arithmetic"] = ("FP32 gather, Boris and deposit weights; FP64 storage and positions; each "
-                                     "tile's current summed in FP32, then added to the FP64 grid; parity 3e-5 "
-                                     "(500 FP32 roundoffs) vs the FP64 oracle (tests/test_gpu_parity.py)")
+        variants[3]["arithmetic"] = ("FP32 gather, Boris and deposit weights; FP64 storage, positions and "
+                                     "current sums; parity 3e-5 (500 FP32 roundoffs) vs the FP64 oracle "
+                                     "(tests/test_gpu_parity.py)")
 
     # ---- static box order (no load balancing: the fixed starting mapping)
     sim = pic.from_workload(wl, stream=stream.cuda_stream)

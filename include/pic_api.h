@@ -343,11 +343,11 @@ pic_status pic_bin_particles(const pic_grid_desc* grid, const double* x, const d
  *                 transformations, ~48-bit significand) for gather, Boris and
  *                 deposit weights, with FP64 storage, positions, index math and
  *                 current accumulation -- the mixed-precision variant; 3 FP32
- *                 for gather, Boris and deposit weights with FP64 storage and
- *                 positions, each tile's current summed in FP32 and then added
- *                 to the FP64 grid (the FP32 variant: about 2^-24 per
- *                 operation, so it meets an FP32-derived tolerance, not the
- *                 FP64 one); 0 keeps the current setting.  The autotuner
+ *                 for gather, Boris and deposit weights with FP64 storage,
+ *                 positions and current accumulation (the FP32 variant:
+ *                 about 2^-24 per operation, so it meets an FP32-derived
+ *                 tolerance, not the FP64 one); 0 keeps the current
+ *                 setting.  The autotuner
  *                 never changes it. */
 typedef struct {
     int threads, ctas_per_sm, split, precision, tile, ppt;

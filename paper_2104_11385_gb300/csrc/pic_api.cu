@@ -168,7 +168,6 @@ void set_tiling(SimDev& h, const int t[3]) {
         h.T[a] = act ? t[a] : 1;
         h.tpb[a] = h.bsz[a] / h.T[a];
         h.ebs[a] = act ? h.T[a] + (h.order == 1 ? 2 : h.order == 2 ? 3 : 4) : 1;
-        h.js[a] = act ? h.T[a] + (h.order == 1 ? 3 : 5) : 1;
     }
     if (h.order == 2) h.ebs[0] += 1;
     h.tiles_per_box = h.tpb[0] * h.tpb[1] * h.tpb[2];

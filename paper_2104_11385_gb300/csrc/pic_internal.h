@@ -73,8 +73,7 @@ struct SimDev {
     int bsz[3];           // box extents in cells
     int tiles_per_box, nboxes, ntiles;
     int ebs[3];           // E/B shared tile extents (x padded to even for TMA)
-    int js[3];            // J shared tile extents
-    int jlo;              // J tile starts jlo cells below the tile origin
+    int jlo;              // a tile's J view starts jlo cells below the tile origin
     double d[3];          // cell sizes
     double nd[3];         // n as doubles (periodic wrap of positions)
     double invd[3];       // 1 / d (0 for the inactive y of 2D runs)

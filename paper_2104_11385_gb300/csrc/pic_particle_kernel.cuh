@@ -8,9 +8,9 @@
 // the guard-extended E/B tile is staged into shared memory by TMA
 // (cp.async.bulk.tensor, local HBM only, no multicast).  The current goes
 // straight into the guard-padded global J arrays as fire-and-forget FP64
-// reductions (red.global.add.f64, performed in L2; the FP64 and float-float
-// variants), or, in the FP32 variant, into a shared-memory FP32 J tile with
-// native shared atomics, flushed once per tile.  Each thread brackets its particle
+// reductions (red.global.add.f64, performed in L2) in every precision; the
+// FP32 variant also stages its particle loads through shared memory with
+// cp.async one loop iteration ahead.  Each thread brackets its particle
 // loop with clock64(); the deltas are warp-reduced, summed in shared memory and
 // added once per unit to the box's cost -- the device-clock cost of
 // arXiv 2104.11385 Sec. 2.2 (Fig. 2a); thread 0 adds the unit's %globaltimer
@@ -481,9 +481,8 @@ __device__ __forceinline__ void stage_hot(HotSim& h, const SimDev& S) {
     }
 }
 
-// Shared-memory layout: six E/B tiles (TMA destinations), three J tiles, and
-// per-warp ring buffers of cell-crossing particles (struct of arrays, WQ
-// slots per warp, up to 8 warps).
+// Per-warp ring buffers of cell-crossing particles (struct of arrays, WQ
+// slots per warp, up to 8 warps per CTA), in global scratch.
 constexpr int WQ = 64;
 constexpr int QMAXWARPS = 8;
 // queue fields: 0 x^n, 1 z^n, 2 x^{n+1}, 3 z^{n+1} (global, unwrapped), 4 q w,
@@ -499,100 +498,88 @@ static_assert(QFields<3>::n * WQ == PIC_RING_DOUBLES && QMAXWARPS == 8,
 struct SmemPlan {
     int eb_stride;  // doubles per E/B component (multiple of 16 -> 128-byte aligned)
     int d_stride;   // doubles per component of the x-difference tile (0: none)
-    int j_stride;   // doubles per J component
-    int eb_vol, d_vol, j_vol;
+    int eb_vol, d_vol;
+    int pb_off;     // doubles from the base to the particle staging buffers
     size_t bytes;
 };
 
-// jshared: the J tile lives in shared memory (FP32 variant); otherwise the
-// current goes to global memory and the J region is empty.  xdiff: the x
-// differences of the staged E/B tile are kept beside it (linear FP64).
-// fcopy: the second region holds the E/B tile converted to floats, with the
-// same component stride in floats (FP32 variant).
-// Layout: E/B tile (TMA) | x differences or float copy | J tile.
-__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], const int js[3], bool jshared, bool xdiff = false,
-                                              bool fcopy = false) {
+// Particle staging (FP32 variant): per warp two buffers of the 7 stored
+// values of 32 particles, filled by cp.async one loop iteration ahead.
+constexpr int PIN_SLOTS = 7 * 32;
+constexpr int PIC_PBUF_DOUBLES = QMAXWARPS * 2 * PIN_SLOTS;
+
+// xdiff: the x differences of the staged E/B tile are kept beside it (linear
+// FP64).  pbuf: particle staging buffers (FP32 variant).  The FP32 variant
+// converts the staged E/B tile in place: for linear shapes to float pairs
+// (F[x], F[x+1] - F[x]), component c at pair c * eb_stride; otherwise to
+// floats, component c at float c * eb_stride.
+// Layout: E/B tile (TMA) | x differences | particle buffers.
+__host__ __device__ inline SmemPlan smem_plan(const int ebs[3], bool xdiff, bool pbuf) {
     SmemPlan p;
     p.eb_vol = ebs[0] * ebs[1] * ebs[2];
     p.d_vol = xdiff ? (ebs[0] - 1) * ebs[1] * ebs[2] : 0;
-    p.j_vol = jshared ? js[0] * js[1] * js[2] : 0;
     p.eb_stride = (p.eb_vol + 15) & ~15;
-    p.d_stride = fcopy ? ((p.eb_stride / 2 + 15) & ~15) : ((p.d_vol + 15) & ~15);
-    p.j_stride = (p.j_vol + 1) & ~1;
-    p.bytes = (size_t)(6 * p.eb_stride + 6 * p.d_stride + 3 * p.j_stride) * sizeof(double);  // tiles only
+    p.d_stride = (p.d_vol + 15) & ~15;
+    p.pb_off = 6 * p.eb_stride + 6 * p.d_stride;
+    p.bytes = (size_t)(p.pb_off + (pbuf ? PIC_PBUF_DOUBLES : 0)) * sizeof(double);  // tiles and buffers
     return p;
 }
 
 // whether a precision / shape order keeps the x-difference tile: FP64 linear
 __host__ __device__ inline bool uses_xdiff(int prec, int order) { return prec == 0 && order == 1; }
 
-template <int DIM, int ORDER, class JT>
-__device__ void flush_j(const SimDev& S, const Tile& tl, const JT* __restrict__ sJ,
-                        const SmemPlan& P) {
-    const int jx = S.js[0], jy = S.js[1];
-    for (int idx = threadIdx.x; idx < 3 * P.j_vol; idx += blockDim.x) {
-        int comp = idx / P.j_vol, r = idx - comp * P.j_vol;
-        double v;
-        if constexpr (std::is_same<JT, float>::value)
-            v = f64_from(sJ[comp * P.j_stride + r]);
-        else
-            v = sJ[comp * P.j_stride + r];
-        if (v == 0.0) continue;
-        int a = r % jx, b = (r / jx) % jy, c = r / (jx * jy);
-        int gx = modi(tl.o[0] - S.jlo + a, S.n[0]);
-        int gy = (DIM == 3) ? modi(tl.o[1] - S.jlo + b, S.n[1]) : 0;
-        int gz = modi(tl.o[2] - S.jlo + c, S.n[2]);
-        atomicAdd(S.F[6 + comp] + pidx(S, gx, gy, gz), v);
-    }
+// double <-> float on the bit patterns without branches: magnitudes below
+// 2^-100 (and zero) become a signed zero (an absolute error below 2^-100,
+// far inside the FP32 variant's tolerance), larger ones round to 24 bits
+__device__ __forceinline__ float f32_of(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long u = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned m = (unsigned)(((u + (1ull << 28)) >> 29) - (896ull << 23));
+    return __uint_as_float(sgn | ((u >> 52) >= 1023 - 100 ? m : 0u));
+}
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+    const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long m = ((unsigned long long)a + (896ull << 23)) << 29;
+    return __longlong_as_double((long long)(sg | (a >= 0x00800000u ? m : 0ull)));
 }
 
-
-// Current accumulation.  FP64 and float-float add each contribution to the
+// Current accumulation.  Every precision adds each contribution to the
 // global FP64 J with red.global.add.f64: the add runs in L2, nothing returns
-// to the SM, and no FP64 instruction is spent on it (a shared-memory FP64
+// to the SM, and no FP64 instruction is spent on it.  (A shared-memory FP64
 // atomic is a compare-and-swap loop whose retries each cost a full-warp FP64
-// add).  A float-float value is renormalised and merged to one double first.
-// The FP32 variant sums into a shared FP32 tile with native shared atomics.
+// add; a shared FP32 atomic add is a compare-and-swap loop as well, measured
+// at about 2.3 tries per add on the foil, and moving the FP32 variant's
+// current from a shared FP32 tile to these reductions took its particle
+// kernel from 895 to 696 us on the 128^3 foil.)  A float-float value is
+// renormalised and merged to one double first; an FP32 value is widened on its
+// bit pattern (subnormal floats, below 2^-126, become zero).
 __device__ __forceinline__ void red_f64(double* p, double v) {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
 }
 __device__ __forceinline__ void jadd(double* p, double v) { red_f64(p, v); }
 __device__ __forceinline__ void jadd(double* p, dd v) { red_f64(p, dd_to_norm(v)); }
-__device__ __forceinline__ void jadd(float* p, float v) { atomicAdd(p, v); }
-
-// element type of the J target: the global FP64 arrays (FP64, float-float),
-// the shared FP32 tile (FP32: its own tolerance covers the FP32 sums)
-template <class R>
-struct JAcc {
-    using type = double;
-    static constexpr bool global = true;
-};
-template <>
-struct JAcc<float> {
-    using type = float;
-    static constexpr bool global = false;
-};
+__device__ __forceinline__ void jadd(double* p, float v) { red_f64(p, f64_of(v)); }
 
 // Where a tile's current goes: base points at component 0 of local node
-// (-jlo, -jlo, -jlo) of the tile (jlo = S.jlo; y is 0 in 2D), cs is the
-// component stride, sy and sz the row and plane strides.  Shared tile: the
-// J tile's own extents.  Global: the padded J arrays, whose guard cells
-// (2 to 4 per side) hold the contributions that fall outside the domain until
-// the fold kernel adds them to their periodic images.
-template <class JT>
+// (-jlo, -jlo, -jlo) of the tile (jlo = S.jlo; y is 0 in 2D) in the padded J
+// arrays, cs is the component stride, sy and sz the row and plane strides.
+// The guard cells (2 to 4 per side) hold the contributions that fall outside
+// the domain until the fold kernel adds them to their periodic images.
 struct JView {
-    JT* base;
+    double* base;
     int64_t cs;
     int sy, sz;
 };
 
-// Esirkepov deposit of one particle into the shared J tile on windows of W
-// nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
+// Esirkepov deposit of one particle into the J arrays (view V) on windows of
+// W nodes per direction.  n*: node supports at x^n, m*: at x^{n+1} (local cells).
 // Prefix sums of DS along each current's own direction times the transverse
 // weight S0a S0b + DSa S0b/2 + S0a DSb/2 + DSa DSb/3 = A_a A_b + DS_a DS_b / 12
 // with A = S0 + DS/2.  qw and vy in R; the prefactors -1/(dA dt) come from jf.
 template <class R, int DIM, int ORDER, int W, class SV>
-__device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R>::type>& V,
+__device__ __forceinline__ bool deposit(const SV& S, const JView& V,
                                         R qw, R vy, const R* jf, const Support<ORDER, R>& n0,
                                         const Support<ORDER, R>& n1, const Support<ORDER, R>& n2,
                                         const Support<ORDER, R>& m0, const Support<ORDER, R>& m1,
@@ -603,10 +590,9 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
     if (DIM == 3) ok = ok && make_window<ORDER, W, R>(n1, m1, wy);
     if (!ok) return false;
     const int sy = V.sy, sz = V.sz, lo = S.jlo;
-    using JT = typename JAcc<R>::type;
-    JT* Jx = V.base;
-    JT* Jy = V.base + V.cs;
-    JT* Jz = V.base + 2 * V.cs;
+    double* Jx = V.base;
+    double* Jy = V.base + V.cs;
+    double* Jz = V.base + 2 * V.cs;
     const R half = A::c(0.5), k12 = A::c(1.0 / 12.0);
     R Ax[W], Az[W], Dx12[W], Dz12[W];
 #pragma unroll
@@ -625,7 +611,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
             Ay[l] = fma(half, wy.DS[l], wy.S0[l]);
             Dy12[l] = k12 * wy.DS[l];
         }
-        JT* origin = V.base + (wz.base + lo) * sz + (wy.base + lo) * sy + (wx.base + lo);
+        double* origin = V.base + (wz.base + lo) * sz + (wy.base + lo) * sy + (wx.base + lo);
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -644,7 +630,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
                 Ac[l] = c == 1 ? Ay[l] : Az[l];
                 Dc12[l] = c == 1 ? Dy12[l] : Dz12[l];
             }
-            JT* Ja = origin + a * V.cs;
+            double* Ja = origin + a * V.cs;
 #pragma unroll 1
             for (int k = 0; k < W; ++k) {
                 R ack = Ac[0], dck = Dc12[0];
@@ -656,7 +642,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const R T = fma(Ab[j], ack, Db[j] * dck);
-                    JT* row = Ja + k * sc + j * sb;
+                    double* row = Ja + k * sc + j * sb;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) jadd(row + l * sa, Pf[l] * T);
                 }
@@ -678,7 +664,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const R T = fma(Ay[j], Az[k], wy.DS[j] * Dz12[k]);
-                    JT* row = Jx + (bz + k) * sz + (by + j) * sy + bx;
+                    double* row = Jx + (bz + k) * sz + (by + j) * sy + bx;
 #pragma unroll
                     for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * T);
                 }
@@ -694,7 +680,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Az[k], wx.DS[i] * Dz12[k]);
-                    JT* col = Jy + (bz + k) * sz + by * sy + (bx + i);
+                    double* col = Jy + (bz + k) * sz + by * sy + (bx + i);
 #pragma unroll
                     for (int j = 0; j < W - 1; ++j) jadd(col + j * sy, Pf[j] * T);
                 }
@@ -710,7 +696,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     const R T = fma(Ax[i], Ay[j], Dx12[i] * wy.DS[j]);
-                    JT* col = Jz + bz * sz + (by + j) * sy + (bx + i);
+                    double* col = Jz + bz * sz + (by + j) * sy + (bx + i);
 #pragma unroll
                     for (int k = 0; k < W - 1; ++k) jadd(col + k * sz, Pf[k] * T);
                 }
@@ -725,7 +711,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
             for (int l = 0; l < W - 1; ++l) { acc = acc + wx.DS[l]; Pf[l] = c * acc; }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                JT* row = Jx + (bz + k) * sz + bx;
+                double* row = Jx + (bz + k) * sz + bx;
 #pragma unroll
                 for (int l = 0; l < W - 1; ++l) jadd(row + l, Pf[l] * Az[k]);
             }
@@ -738,7 +724,7 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
             for (int k = 0; k < W - 1; ++k) { acc = acc + wz.DS[k]; Pf[k] = c * acc; }
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                JT* col = Jz + bz * sz + (bx + i);
+                double* col = Jz + bz * sz + (bx + i);
 #pragma unroll
                 for (int k = 0; k < W - 1; ++k) jadd(col + k * sz, Pf[k] * Ax[i]);
             }
@@ -761,12 +747,12 @@ __device__ __forceinline__ bool deposit(const SV& S, const JView<typename JAcc<R
 // A_a A_b +- d_a d_b / 12 (A = (1 - m, m), m = f0 + d/2).  Same weights as
 // deposit<R, DIM, 1, 2>, with fewer instructions.
 template <class R, int DIM, class SV>
-__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<typename JAcc<R>::type>& V,
+__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView& V,
                                                      R qw, R vy, const R* jf, const Support<1, R>* n,
                                                      const R* disp);
 
 template <class R, int DIM, class SV>
-__device__ __forceinline__ void deposit_lin_incell(const SV& S, const JView<typename JAcc<R>::type>& V,
+__device__ __forceinline__ void deposit_lin_incell(const SV& S, const JView& V,
                                                    R qw, R vy, const R* jf,
                                                    const Support<1, R>* n, const Support<1, R>* m) {
     const R disp[3] = {m[0].w[1] - n[0].w[1], m[1].w[1] - n[1].w[1], m[2].w[1] - n[2].w[1]};
@@ -776,16 +762,15 @@ __device__ __forceinline__ void deposit_lin_incell(const SV& S, const JView<type
 // the same deposit, given the in-cell displacement disp[a] = x^{n+1} - x^n
 // (cells) of each direction
 template <class R, int DIM, class SV>
-__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<typename JAcc<R>::type>& V,
+__device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView& V,
                                                      R qw, R vy, const R* jf, const Support<1, R>* n,
                                                      const R* disp) {
     using A = Arith<R>;
     const R k12 = A::c(1.0 / 12.0), half = A::c(0.5), one = A::c(1.0);
     const int sy = V.sy, sz = V.sz, lo = S.jlo;
-    using JT = typename JAcc<R>::type;
-    JT* Jx = V.base;
-    JT* Jy = V.base + V.cs;
-    JT* Jz = V.base + 2 * V.cs;
+    double* Jx = V.base;
+    double* Jy = V.base + V.cs;
+    double* Jz = V.base + 2 * V.cs;
     const R dx = disp[0], dz = disp[2];
     const R mx = fma(half, dx, n[0].w[1]), mz = fma(half, dz, n[2].w[1]);
     const R ax0 = one - mx, az0 = one - mz;
@@ -796,7 +781,7 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
         const R my = fma(half, dy, n[1].w[1]);
         const R ay0 = one - my;
         const int by = n[1].s + lo;
-        JT* origin = V.base + bz * sz + by * sy + bx;
+        double* origin = V.base + bz * sz + by * sy + bx;
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
             const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -806,7 +791,7 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
             const R ab = b == 0 ? ax0 : ay0, ac = c == 1 ? ay0 : az0;
             const R e = (db * dc) * k12;
             const R pf = -((qw * pick3(a, jf[0], jf[1], jf[2])) * pick3(a, dx, dy, dz));
-            JT* r = origin + a * V.cs;
+            double* r = origin + a * V.cs;
             jadd(r, pf * fma(ab, ac, e));
             jadd(r + sb, pf * fma(mb, ac, -e));
             jadd(r + sc, pf * fma(ab, mc, -e));
@@ -826,7 +811,7 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
             const R q = qw * jf[0];
             const R pf = -(q * dx), pe = -(q * d3);
             const R p1 = pf * my, p0 = pf - p1;
-            JT* r = Jx + bz * sz + by * sy + bx;
+            double* r = Jx + bz * sz + by * sy + bx;
             jadd(r, fma(p0, az0, pe));
             jadd(r + sy, fma(p1, az0, -pe));
             jadd(r + sz, fma(p0, mz, -pe));
@@ -836,7 +821,7 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
             const R q = qw * jf[1];
             const R pf = -(q * dy), pe = -(q * d3);
             const R p1 = pf * mx, p0 = pf - p1;
-            JT* r = Jy + bz * sz + by * sy + bx;
+            double* r = Jy + bz * sz + by * sy + bx;
             jadd(r, fma(p0, az0, pe));
             jadd(r + 1, fma(p1, az0, -pe));
             jadd(r + sz, fma(p0, mz, -pe));
@@ -846,7 +831,7 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
             const R q = qw * jf[2];
             const R pf = -(q * dz), pe = -(q * d3);
             const R p1 = pf * mx, p0 = pf - p1;
-            JT* r = Jz + bz * sz + by * sy + bx;
+            double* r = Jz + bz * sz + by * sy + bx;
             jadd(r, fma(p0, ay0, pe));
             jadd(r + 1, fma(p1, ay0, -pe));
             jadd(r + sy, fma(p0, my, -pe));
@@ -855,20 +840,20 @@ __device__ __forceinline__ void deposit_lin_incell_d(const SV& S, const JView<ty
     } else {
         {   // Jx at (bx, bz + k): -(q w/(dz dt)) DSx A_z
             const R pf = -((qw * jf[0]) * dx);
-            JT* r = Jx + bz * sz + bx;
+            double* r = Jx + bz * sz + bx;
             jadd(r, pf * az0);
             jadd(r + sz, pf * mz);
         }
         {   // Jz at (bx + i, bz)
             const R pf = -((qw * jf[2]) * dz);
-            JT* r = Jz + bz * sz + bx;
+            double* r = Jz + bz * sz + bx;
             jadd(r, pf * ax0);
             jadd(r + 1, pf * mx);
         }
         {   // out-of-plane Jy at (bx + i, bz + k)
             const R e = (dx * dz) * k12;
             const R c = qw * vy * jf[1];
-            JT* r = Jy + bz * sz + bx;
+            double* r = Jy + bz * sz + bx;
             jadd(r, c * fma(ax0, az0, e));
             jadd(r + 1, c * fma(mx, az0, -e));
             jadd(r + sz, c * fma(ax0, mz, -e));
@@ -897,13 +882,34 @@ __device__ __forceinline__ PIn load_one(const SPV& sp, int64_t p) {
     return in;
 }
 
+// The same values staged through shared memory: the lane's column of a
+// staging buffer (value a of the particle at slot[32 a]), filled by cp.async
+template <int DIM, class SPV>
+__device__ __forceinline__ void stage_in(const SPV& sp, int64_t p, double* slot) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+        if (DIM == 3 || a != 1) cp_async_8(slot + 32 * a, sp.cur[a] + p);
+}
+template <int DIM>
+__device__ __forceinline__ PIn read_staged(const double* slot) {
+    PIn in;
+    in.X = slot[0];
+    in.Y = (DIM == 3) ? slot[32] : 0.0;
+    in.Z = slot[64];
+    in.u0 = slot[96];
+    in.u1 = slot[128];
+    in.u2 = slot[160];
+    in.w = slot[192];
+    return in;
+}
+
 // Gather, Boris push, and deposit of one particle.  Particles that keep their
 // support in every direction deposit at once on the small window; the others
 // go to the warp's ring buffer, drained 32 at a time by drain_warp.
 template <class R, int DIM, int ORDER, class SV, class SPV>
 __device__ __forceinline__ void push_one(const SV& S, const SPV& sp, const Tile& tl,
                                          const R* __restrict__ sEB, const R* __restrict__ sD,
-                                         const JView<typename JAcc<R>::type>& V,
+                                         const JView& V,
                                          double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                          const R* jf, const R* dtd, R kq, R qs, int64_t p, const PIn& in,
                                          int32_t* err) {
@@ -1046,27 +1052,44 @@ __device__ __forceinline__ double unfix24(long long b) {
 }
 __device__ __forceinline__ float frac24(long long b) { return (float)(int)(b & 0xFFFFFFll) * 5.9604644775390625e-8f; }
 
-// double <-> float on the bit patterns without branches: magnitudes below
-// 2^-100 (and zero) become a signed zero (an absolute error below 2^-100,
-// far inside the FP32 variant's tolerance), larger ones round to 24 bits
-__device__ __forceinline__ float f32_of(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long u = b & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-    const unsigned m = (unsigned)(((u + (1ull << 28)) >> 29) - (896ull << 23));
-    return __uint_as_float(sgn | ((u >> 52) >= 1023 - 100 ? m : 0u));
+// Linear FP32 gather from the staged tile held as pairs (F[x], F[x+1] - F[x])
+// of floats: each x lerp is one 8-byte shared load and one FMA, and gives the
+// same float as a + f (b - a) on the two floats.  Component c starts at pair
+// c * stride.
+template <int DIM>
+__device__ __forceinline__ float interp_pairs(const float2* __restrict__ F, int SX, int SY, const Support<1, float>& sx,
+                                              const Support<1, float>& sy, const Support<1, float>& sz) {
+    constexpr int H = EBHalo<1>::lo;
+    auto lerp = [](float a, float b, float f) { return fmaf(f, b - a, a); };
+    const float fx = sx.w[1];
+    if constexpr (DIM == 3) {
+        const float2* r = F + ((sz.s + H) * SY + (sy.s + H)) * SX + (sx.s + H);
+        const float2 p00 = r[0], p10 = r[SX], p01 = r[SX * SY], p11 = r[SX * SY + SX];
+        const float a00 = fmaf(fx, p00.y, p00.x), a10 = fmaf(fx, p10.y, p10.x);
+        const float a01 = fmaf(fx, p01.y, p01.x), a11 = fmaf(fx, p11.y, p11.x);
+        return lerp(lerp(a00, a10, sy.w[1]), lerp(a01, a11, sy.w[1]), sz.w[1]);
+    } else {
+        const float2* r = F + (sz.s + H) * SX + (sx.s + H);
+        const float2 p0 = r[0], p1 = r[SX];
+        return lerp(fmaf(fx, p0.y, p0.x), fmaf(fx, p1.y, p1.x), sz.w[1]);
+    }
 }
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
-    const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
-    const unsigned long long m = ((unsigned long long)a + (896ull << 23)) << 29;
-    return __longlong_as_double((long long)(sg | (a >= 0x00800000u ? m : 0ull)));
+template <int DIM>
+__device__ __forceinline__ void gather6_pairs(const float2* __restrict__ sP, int stride, int SX, int SY,
+                                              const Support<1, float>* nd, const Support<1, float>* hf, float* e,
+                                              float* b) {
+    e[0] = interp_pairs<DIM>(sP, SX, SY, hf[0], nd[1], nd[2]);
+    e[1] = interp_pairs<DIM>(sP + stride, SX, SY, nd[0], hf[1], nd[2]);
+    e[2] = interp_pairs<DIM>(sP + 2 * stride, SX, SY, nd[0], nd[1], hf[2]);
+    b[0] = interp_pairs<DIM>(sP + 3 * stride, SX, SY, nd[0], hf[1], hf[2]);
+    b[1] = interp_pairs<DIM>(sP + 4 * stride, SX, SY, hf[0], nd[1], hf[2]);
+    b[2] = interp_pairs<DIM>(sP + 5 * stride, SX, SY, hf[0], hf[1], nd[2]);
 }
 
 // gather, Boris push and deposit of one particle, FP32 arithmetic, linear shapes
 template <int DIM, class SV, class SPV>
 __device__ __forceinline__ void push_one_f32lin(const SV& S, const SPV& sp, const Tile& tl,
-                                                const float* __restrict__ sEB, const JView<float>& V,
+                                                const float* __restrict__ sEB, const JView& V,
                                                 double* __restrict__ sQw, unsigned* s_tail, const SmemPlan& P,
                                                 const float* jf, const float* dtd, float kq, float qs,
                                                 int64_t p, const PIn& in, int32_t* err) {
@@ -1118,7 +1141,7 @@ __device__ __forceinline__ void push_one_f32lin(const SV& S, const SPV& sp, cons
         }
     }
     float ev[3], bv[3];
-    gather6<float, 1, DIM>(sEB, P.eb_stride, S.ebs[0], S.ebs[1], nd, hf, ev, bv);
+    gather6_pairs<DIM>(reinterpret_cast<const float2*>(sEB), P.eb_stride, S.ebs[0], S.ebs[1], nd, hf, ev, bv);
     const float u0 = f32_of(in.u0), u1 = f32_of(in.u1), u2 = f32_of(in.u2);
     const float qw = qs * f32_of(in.w);
 
@@ -1211,7 +1234,7 @@ __device__ __forceinline__ void push_one_f32lin(const SV& S, const SPV& sp, cons
 // entries hold global positions), so rings then drain across tile changes.
 template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl,
-                                           const JView<typename JAcc<R>::type>& V,
+                                           const JView& V,
                                            const double* __restrict__ sQw, unsigned head, unsigned n,
                                            const R* jf, int32_t* err) {
     using A = Arith<R>;
@@ -1245,14 +1268,14 @@ __device__ __forceinline__ void drain_warp(const SimDev& S, const Tile& tl,
 // (about 5 % of the kernel); FP64 is indifferent and inlines it, as does FP32
 template <class R, int DIM, int ORDER>
 __device__ __noinline__ void drain_warp_outlined(const SimDev& S, const Tile& tl,
-                                                 const JView<typename JAcc<R>::type>& V,
+                                                 const JView& V,
                                                  const double* __restrict__ sQw, unsigned head, unsigned n,
                                                  const R* jf, int32_t* err) {
     drain_warp<R, DIM, ORDER>(S, tl, V, sQw, head, n, jf, err);
 }
 
 template <class R, int DIM, int ORDER>
-__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, const JView<typename JAcc<R>::type>& V,
+__device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, const JView& V,
                                       const double* __restrict__ sQw, unsigned head, unsigned n,
                                       const R* jf, int32_t* err) {
     if constexpr (!std::is_same<R, dd>::value)
@@ -1261,23 +1284,14 @@ __device__ __forceinline__ void drain(const SimDev& S, const Tile& tl, const JVi
         drain_warp_outlined<R, DIM, ORDER>(S, tl, V, sQw, head, n, jf, err);
 }
 
-// the J view of tile tl: the shared FP32 tile, or the global padded arrays
-template <class JT>
-__device__ __forceinline__ JView<JT> j_view(const SimDev& S, const Tile& tl, JT* sJ, const SmemPlan& P) {
-    JView<JT> v;
-    if constexpr (JAcc<JT>::global) {
-        const int lo = S.jlo;
-        v.base = reinterpret_cast<JT*>(S.F[6]) +
-                 pidx(S, tl.o[0] - lo, S.dim == 3 ? tl.o[1] - lo : 0, tl.o[2] - lo);
-        v.cs = (int64_t)S.pn[0] * S.pn[1] * S.pn[2];
-        v.sy = S.pn[0];
-        v.sz = S.pn[0] * S.pn[1];
-    } else {
-        v.base = sJ;
-        v.cs = P.j_stride;
-        v.sy = S.js[0];
-        v.sz = S.js[0] * S.js[1];
-    }
+// the J view of tile tl: the global padded arrays
+__device__ __forceinline__ JView j_view(const SimDev& S, const Tile& tl) {
+    JView v;
+    const int lo = S.jlo;
+    v.base = S.F[6] + pidx(S, tl.o[0] - lo, S.dim == 3 ? tl.o[1] - lo : 0, tl.o[2] - lo);
+    v.cs = (int64_t)S.pn[0] * S.pn[1] * S.pn[2];
+    v.sy = S.pn[0];
+    v.sz = S.pn[0] * S.pn[1];
     return v;
 }
 
@@ -1305,20 +1319,18 @@ struct SimConsts {
 // MINB = resident CTAs per SM the register allocation is sized for (1: up to
 // 255 registers, 8 warps per SM; 2: at most 128 registers, 16 warps per SM).
 // PREC = arithmetic of the particle push: 0 FP64, 1 float-float, 2 FP32 (storage,
-// positions and index math stay FP64 in all three; the current goes to the
-// global FP64 J by L2 reductions, except in the FP32 variant, whose shared
-// tile sums in FP32).
+// positions and index math stay FP64 in all three, and the current goes to the
+// global FP64 J by L2 reductions).
 // PPT = particles per thread per loop iteration: their HBM loads are issued
-// together before the first of them is pushed.
+// together before the first of them is pushed (FP32 with PPT 1 stages each
+// lane's next particle through shared memory instead).
 template <int DIM, int ORDER, int MINB, int PREC, int PPT>
 __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev* __restrict__ sd,
                                                               SimDev* __restrict__ sims) {
     using R = typename std::conditional<PREC == 1, dd, typename std::conditional<PREC == 2, float, double>::type>::type;
     using A = Arith<R>;
-    using JT = typename JAcc<R>::type;
-    constexpr bool GJ = JAcc<R>::global;
     constexpr bool XD = PREC == 0 && ORDER == 1;  // x-difference tile beside the E/B tile
-    constexpr bool FC = PREC == 2;                // float copy of the E/B tile beside it
+    constexpr bool FC = PREC == 2;                // E/B tile converted to floats in place; particle staging
     extern __shared__ __align__(128) double smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -1350,21 +1362,18 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
     // drain runs once per 32 crossings)
     double* const gring = sd->rings + ((size_t)blockIdx.x * QMAXWARPS + warp) * PIC_RING_DOUBLES;
 
-    // global J target: a warp's ring of cell-crossing particles outlives tile
-    // changes; it is drained when the simulation changes (rings hold one
-    // simulation's particles, at that simulation's queue offset) and at the end
+    // a warp's ring of cell-crossing particles outlives tile changes (with the
+    // global J every tile gives the same global nodes); it is drained when the
+    // simulation changes (rings hold one simulation's particles, at that
+    // simulation's queue offset) and at the end
     auto drain_ring = [&](const SimDev& CS) {
-        if constexpr (GJ) {
-            const unsigned head = s_qhead[warp], tail = s_qtail[warp];
-            if (tail != head) {
-                const SmemPlan CP = smem_plan(CS.ebs, CS.js, false, XD, FC);
-                const SimConsts<R, DIM> K(CS);
-                drain<R, DIM, ORDER>(CS, cur, j_view<JT>(CS, cur, nullptr, CP), gring, head, tail - head, K.jf,
-                                     sd->err);
-                __syncwarp();
-                if (lane == 0) s_qhead[warp] = tail;
-                __syncwarp();
-            }
+        const unsigned head = s_qhead[warp], tail = s_qtail[warp];
+        if (tail != head) {
+            const SimConsts<R, DIM> K(CS);
+            drain<R, DIM, ORDER>(CS, cur, j_view(CS, cur), gring, head, tail - head, K.jf, sd->err);
+            __syncwarp();
+            if (lane == 0) s_qhead[warp] = tail;
+            __syncwarp();
         }
     };
 
@@ -1391,12 +1400,10 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
         const SimDev& S = sims[unit.sim];
         const bool cap_clk = (S.capture & 1) != 0, cap_time = (S.capture & 2) != 0;
         const uint64_t t_unit0 = (threadIdx.x == 0 && cap_time) ? globaltimer() : 0ull;
-        const SmemPlan P = smem_plan(S.ebs, S.js, !GJ, XD, FC);
+        const SmemPlan P = smem_plan(S.ebs, XD, FC);
         double* sEBd = smem;
-        double* sDd = smem + 6 * P.eb_stride;   // x differences (linear FP64), float copy (FP32)
-        const R* sEB = reinterpret_cast<const R*>(FC ? sDd : smem);
-        double* sJd = sDd + 6 * P.d_stride;     // J tile (FP32 variant only)
-        JT* sJ = reinterpret_cast<JT*>(sJd);
+        double* sDd = smem + 6 * P.eb_stride;   // x differences (linear FP64)
+        const R* sEB = reinterpret_cast<const R*>(smem);
         unsigned long long my_clk = 0ull;
         const SimConsts<R, DIM> K(S);
 
@@ -1414,17 +1421,8 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                 const int64_t s0 = max(sp.off[t], r0), s1 = min(sp.off[t + 1], r1);
                 if (s0 >= s1) continue;
                 if (t != cur.t || unit.sim != cur.sim) {
-                    if (GJ && cur.t >= 0 && unit.sim != cur.sim) drain_ring(sims[cur.sim]);
+                    if (cur.t >= 0 && unit.sim != cur.sim) drain_ring(sims[cur.sim]);
                     __syncthreads();
-                    if constexpr (!GJ) {
-                        if (cur.t >= 0) {
-                            const SimDev& CS = sims[cur.sim];
-                            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD, FC);
-                            flush_j<DIM, ORDER>(CS, cur,
-                                                reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
-                            __syncthreads();
-                        }
-                    }
                     cur.sim = unit.sim;
                     cur.t = t;
                     tile_origin(S, t, cur.o);
@@ -1439,8 +1437,6 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         for (int c = 0; c < 6; ++c)
                             tma_load_3d(sEBd + c * P.eb_stride, &S.tmap[c], x0, y0, z0, &bar);
                     }
-                    if constexpr (!GJ)
-                        for (int i = threadIdx.x; i < 3 * P.j_stride; i += blockDim.x) sJd[i] = 0.0;
                     bool ok = mbar_wait_bounded(&bar, phase);
                     phase ^= 1u;
                     if (!ok) {
@@ -1480,59 +1476,102 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                         __syncthreads();
                     }
                     if constexpr (PREC == 2) {
-                        // E/B tile to FP32 in the float-copy region, one pass
-                        float* sEBf = reinterpret_cast<float*>(sDd);
-                        const int ntot = 6 * P.eb_stride;
-                        for (int i = threadIdx.x; i < ntot; i += blockDim.x) sEBf[i] = f32_of(sEBd[i]);
+                        // E/B tile to FP32 in place, in rounds of 8 elements per thread
+                        // (nt threads); round m reads doubles [8 nt m, 8 nt (m + 1)] and,
+                        // after its barrier, writes elements [8 nt m, 8 nt (m + 1)).
+                        // Linear shapes: element i becomes the float pair (F[i],
+                        // F[i+1] - F[i]) in the 8 bytes of double i (the pair at the end
+                        // of a row is never read).  Other orders: element i becomes float
+                        // i, overlaying doubles [4 nt m, 4 nt (m + 1)).  Either way a
+                        // round writes only doubles read by rounds <= m and none read by a
+                        // later round.
+                        const int ntot = 6 * P.eb_stride, nt = blockDim.x;
+                        for (int r0 = 0; r0 < ntot; r0 += 8 * nt) {
+                            float v[8], d[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int i = r0 + k * nt + threadIdx.x;
+                                v[k] = i < ntot ? f32_of(sEBd[i]) : 0.0f;
+                                if constexpr (ORDER == 1) d[k] = i + 1 < ntot ? f32_of(sEBd[i + 1]) - v[k] : 0.0f;
+                            }
+                            __syncthreads();
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int i = r0 + k * nt + threadIdx.x;
+                                if (i < ntot) {
+                                    if constexpr (ORDER == 1)
+                                        reinterpret_cast<float2*>(sEBd)[i] = make_float2(v[k], d[k]);
+                                    else
+                                        reinterpret_cast<float*>(sEBd)[i] = v[k];
+                                }
+                            }
+                        }
                         __syncthreads();
                     }
                 }
                 const unsigned long long c0 = cap_clk ? clock64() : 0ull;
                 {
                     // per-warp loop: no CTA barrier until the tile changes
-                    const JView<JT> V = j_view<JT>(S, cur, sJ, P);
+                    const JView V = j_view(S, cur);
                     double* sQw = gring;
                     const R* sD = XD ? reinterpret_cast<const R*>(sDd) : nullptr;
                     volatile unsigned* vtail = s_qtail + warp;
-                    for (int64_t p0 = s0 + warp * (32 * PPT); p0 < s1; p0 += (int64_t)blockDim.x * PPT) {
-                        PIn in[PPT];
-#pragma unroll
-                        for (int q = 0; q < PPT; ++q) {
-                            const int64_t p = p0 + q * 32 + lane;
-                            if (p < s1) in[q] = load_one<DIM>(s_hot.sp[spi], p);
-                        }
-#pragma unroll
-                        for (int q = 0; q < PPT; ++q) {
-                            const int64_t p = p0 + q * 32 + lane;
-                            if (p < s1) {
-                                if constexpr (PREC == 2 && ORDER == 1)
-                                    push_one_f32lin<DIM>(s_hot, s_hot.sp[spi], cur, sEB, V, sQw, s_qtail + warp, P,
-                                                         K.jf, K.dtd, kq, qs, p, in[q], sd->err);
-                                else
-                                    push_one<R, DIM, ORDER>(s_hot, s_hot.sp[spi], cur, sEB, sD, V, sQw, s_qtail + warp,
-                                                            P, K.jf, K.dtd, kq, qs, p, in[q], sd->err);
-                            }
+                    auto push = [&](int64_t p, const PIn& in) {
+                        if constexpr (PREC == 2 && ORDER == 1)
+                            push_one_f32lin<DIM>(s_hot, s_hot.sp[spi], cur, sEB, V, sQw, s_qtail + warp, P, K.jf,
+                                                 K.dtd, kq, qs, p, in, sd->err);
+                        else
+                            push_one<R, DIM, ORDER>(s_hot, s_hot.sp[spi], cur, sEB, sD, V, sQw, s_qtail + warp, P,
+                                                    K.jf, K.dtd, kq, qs, p, in, sd->err);
+                    };
+                    // a full ring (32 queued crossings) is drained by the whole warp
+                    auto drain_full = [&]() {
+                        __syncwarp();
+                        const unsigned head = s_qhead[warp], tail = *vtail;
+                        if (tail - head >= 32u) {
+                            drain<R, DIM, ORDER>(S, cur, V, sQw, head, 32u, K.jf, sd->err);
                             __syncwarp();
-                            const unsigned head = s_qhead[warp], tail = *vtail;
-                            if (tail - head >= 32u) {
-                                drain<R, DIM, ORDER>(S, cur, V, sQw, head, 32u, K.jf, sd->err);
-                                __syncwarp();
-                                if (lane == 0) s_qhead[warp] = head + 32u;
-                                __syncwarp();
+                            if (lane == 0) s_qhead[warp] = head + 32u;
+                            __syncwarp();
+                        }
+                    };
+                    if constexpr (PREC == 2 && PPT == 1) {
+                        // FP32: the particle loads are the latency the loop waits on; each
+                        // lane stages its next particle into shared memory with cp.async
+                        // one iteration ahead (two buffers per warp, the lane's own column)
+                        double* const pbw = smem + P.pb_off + warp * (2 * PIN_SLOTS) + lane;
+                        const int64_t pf = s0 + warp * 32 + lane;
+                        if (pf < s1) stage_in<DIM>(s_hot.sp[spi], pf, pbw);
+                        cp_async_commit();
+                        unsigned buf = 0u;
+                        for (int64_t p0 = s0 + warp * 32; p0 < s1; p0 += (int64_t)blockDim.x) {
+                            const int64_t pn = p0 + blockDim.x + lane;
+                            if (pn < s1) stage_in<DIM>(s_hot.sp[spi], pn, pbw + (buf ^ 1u) * PIN_SLOTS);
+                            cp_async_commit();
+                            cp_async_wait<1>();
+                            const int64_t p = p0 + lane;
+                            if (p < s1) push(p, read_staged<DIM>(pbw + buf * PIN_SLOTS));
+                            buf ^= 1u;
+                            drain_full();
+                        }
+                        cp_async_wait<0>();
+                    } else {
+                        for (int64_t p0 = s0 + warp * (32 * PPT); p0 < s1; p0 += (int64_t)blockDim.x * PPT) {
+                            PIn in[PPT];
+#pragma unroll
+                            for (int q = 0; q < PPT; ++q) {
+                                const int64_t p = p0 + q * 32 + lane;
+                                if (p < s1) in[q] = load_one<DIM>(s_hot.sp[spi], p);
+                            }
+#pragma unroll
+                            for (int q = 0; q < PPT; ++q) {
+                                const int64_t p = p0 + q * 32 + lane;
+                                if (p < s1) push(p, in[q]);
+                                drain_full();
                             }
                         }
                     }
                     __syncwarp();
-                    if constexpr (!GJ) {
-                        // the shared tile is flushed at the tile change: drain the ring now
-                        const unsigned head = s_qhead[warp], tail = *vtail;
-                        if (tail != head) {
-                            drain<R, DIM, ORDER>(S, cur, V, sQw, head, tail - head, K.jf, sd->err);
-                            __syncwarp();
-                            if (lane == 0) s_qhead[warp] = tail;
-                        }
-                        __syncwarp();
-                    }
                 }
                 if (cap_clk) my_clk += clock64() - c0;
             }
@@ -1552,16 +1591,7 @@ __global__ void __launch_bounds__(256, MINB) pic_particle_kernel(const SchedDev*
                           (unsigned long long)(globaltimer() - t_unit0));
         }
     }
-    if (cur.t >= 0) {
-        if constexpr (GJ) {
-            drain_ring(sims[cur.sim]);
-        } else {
-            __syncthreads();
-            const SimDev& CS = sims[cur.sim];
-            const SmemPlan CP = smem_plan(CS.ebs, CS.js, true, XD, FC);
-            flush_j<DIM, ORDER>(CS, cur, reinterpret_cast<const JT*>(smem + 6 * CP.eb_stride + 6 * CP.d_stride), CP);
-        }
-    }
+    if (cur.t >= 0) drain_ring(sims[cur.sim]);
 }
 
 // ---- host side of one precision: launch, attributes, occupancy

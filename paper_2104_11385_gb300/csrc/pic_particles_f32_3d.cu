@@ -1,4 +1,4 @@
-// pic_particles_f32_3d.cu -- FP32 instantiation of the particle kernel (the FP32 variant: FP64 storage and positions, FP32 gather, push, deposit weights and tile sums), 3D shapes of order 1-3.
+// pic_particles_f32_3d.cu -- FP32 instantiation of the particle kernel (the FP32 variant: FP64 storage and positions, FP32 gather, push and deposit weights, FP64 current sums), 3D shapes of order 1-3.
 #define PIC_PREC 2
 #define PIC_DIM 3
 #include "pic_particle_kernel.cuh"

@@ -6,15 +6,14 @@
 PIC_DEFINE_PARTICLE_TU(p0_d3)
 
 size_t pic_particle_smem_bytes(int dim, int order, const int T[3], int threads, int prec) {
-    int ebs[3], js[3];
+    int ebs[3];
     for (int a = 0; a < 3; ++a) {
         bool act = !(dim == 2 && a == 1);
         ebs[a] = act ? T[a] + (order == 1 ? 2 : order == 2 ? 3 : 4) : 1;
-        js[a] = act ? T[a] + (order == 1 ? 3 : 5) : 1;
     }
     if (order == 2) ebs[0] += 1;  // even x extent for TMA (16-byte rows)
-    // tiles (the x differences for linear FP64; the float copy of the E/B
-    // tile and the J tile for the FP32 variant, prec 2) + alignment slack of
-    // the dynamic base; the rings of crossing particles are in global memory
-    return smem_plan(ebs, js, prec == 2, uses_xdiff(prec, order), prec == 2).bytes + 128;
+    // tiles (the x differences for linear FP64; the particle staging buffers
+    // for the FP32 variant, prec 2) + alignment slack of the dynamic base; the
+    // rings of crossing particles are in global memory
+    return smem_plan(ebs, uses_xdiff(prec, order), prec == 2).bytes + 128;
 }

@@ -1,6 +1,7 @@
 // pic_sync.cuh -- device-side synchronisation helpers shared by the particle
 // kernel and the self-test of its bounded wait: shared-memory addresses,
-// %globaltimer, and mbarrier init / expect-tx / bounded wait (inline PTX).
+// %globaltimer, mbarrier init / expect-tx / bounded wait, and cp.async copies
+// with their group waits (inline PTX).
 #pragma once
 #include <cstdint>
 
@@ -50,6 +51,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
             else if (now - t0 > limit_ns) return false;
         }
     }
+}
+
+}  // namespace
+
+namespace {
+
+// Ampere-style asynchronous copies global -> shared (cp.async, 8 bytes per
+// thread): the copy completes without the issuing thread waiting, and
+// cp.async.wait_group makes the thread's own earlier groups visible to it.
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)),
+                 "l"(__cvta_generic_to_global(gmem_src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 }  // namespace

@@ -31,7 +31,9 @@ extern "C" {
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture begins.  The address is kept per device and
  *     CUDA context: after a device reset (cudaDeviceReset) the next call looks
- *     it up again, so that call too belongs outside a capture.
+ *     it up again, so that call too belongs outside a capture.  Later calls
+ *     issue only a memset and kernel launches on grid->stream and can be
+ *     captured into a CUDA graph (global capture mode) and replayed.
  *   - Every call, on every stream, shares the one array, and it keeps the last
  *     call's contents; each call zeroes the part it uses on its stream first.
  *     Calls whose device work overlaps (different streams, or host threads

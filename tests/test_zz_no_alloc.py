@@ -70,3 +70,35 @@ def test_noalloc_rejects_more_boxes_than_its_scratch():
         S.bin_particles(3, n, (1, 1, 1), (1.0, 1.0, 1.0), x, x, x, off, perm, fn="pic_bin_particles_noalloc")
     assert ei.value.status == L.PIC_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_call_captured_in_a_cuda_graph():
+    """The call allocates and synchronises nothing, so once its first call on
+    the device has run (the scratch address lookup), it can be captured into a
+    CUDA graph in the global capture mode; the graph's replays give the
+    allocating call's result, also after the inputs are rewritten in place."""
+    import torch
+    from paper_2104_11385_gb300 import sim as S
+    dim, n, box, dx, npart = 3, (32, 32, 32), (8, 8, 8), (0.25, 0.25, 0.25), 100_000
+    nb = int(np.prod([n[a] // box[a] for a in range(3)]))
+    x, y, z = _inputs(7, dim, n, box, dx, npart)
+    off = torch.full((nb + 1,), -7, dtype=torch.int64, device="cuda")
+    perm = torch.full((npart,), -7, dtype=torch.int64, device="cuda")
+    S.bin_particles(dim, n, box, dx, x, y, z, off, perm, fn="pic_bin_particles_noalloc")  # outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.bin_particles(dim, n, box, dx, x, y, z, off, perm, stream=torch.cuda.current_stream().cuda_stream,
+                        fn="pic_bin_particles_noalloc")
+    for seed in (7, 8):
+        if seed != 7:
+            x2, y2, z2 = _inputs(seed, dim, n, box, dx, npart)
+            x.copy_(x2)
+            y.copy_(y2)
+            z.copy_(z2)
+        ref = _run("pic_bin_particles", dim, n, box, dx, x, y, z)
+        off.fill_(-7)
+        perm.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        _same((off.cpu().numpy(), perm.cpu().numpy()), ref)

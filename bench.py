@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 # FP64 peak from unit counts and clocks, for context beside the measured one:
 # SMs x 2 DFMA lanes/clk/SM x 2 flop x 2.07 GHz (the SM count read from the device)
 FP64_LANES_PER_SM_CLK = 2
@@ -121,6 +122,8 @@ def parse():
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--no-cost-arms", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="K-step windows timed on the balanced arm for the spread (median, best) beside the value")
     ap.add_argument("--static-steps", type=int, default=5,
                     help="timed steps of the no-balancing arm (about 8x slower per step than the balanced one)")
     ap.add_argument("--server-requests", type=int, default=1000)
@@ -318,6 +321,9 @@ def run_ours(args, rank, world, wl=None, full=True):
         ms_bal = timed(sim, args.steps)
     clocks = cs.summary()
     lb_timed = sim.lb_log()[nlog0:]  # the load-balancing calls made inside the timed steps
+    # spread of the step time: the same K-step window again (the line's value is
+    # the first window, timed as the contract says; these are beside it)
+    reps = [ms_bal / args.steps] + [timed(sim, args.steps) / args.steps for _ in range(max(0, args.repeats - 1))]
     # kernel-level timing: the same number of steps again, with CUDA events on
     # the library's stream around each launch
     st = profiled(sim, args.steps)
@@ -364,7 +370,12 @@ def run_ours(args, rank, world, wl=None, full=True):
               "speedup_balanced_over_static": (ms_static / ks) / (ms_bal / args.steps),
               "what": "mode NONE: one unit per box, fixed equal-count Morton mapping, per-worker lists"}
 
-    out = {"value": rate(ms_bal, args.steps), "ms_per_step": ms_bal / args.steps, "clocks": clocks,
+    srt = sorted(reps)
+    spread = {"windows": len(reps), "steps_per_window": args.steps, "median_ms_per_step": srt[len(srt) // 2],
+              "best_ms_per_step": srt[0], "worst_ms_per_step": srt[-1],
+              "median_value": rate(srt[len(srt) // 2] * args.steps, args.steps)}
+    out = {"value": rate(ms_bal, args.steps), "ms_per_step": ms_bal / args.steps, "step_time_spread": spread,
+           "clocks": clocks,
            "gpu_launches": int(round(kernels_per_step * args.steps)), "static_order": static,
            "mixed_precision": variants.get(2), "fp32": variants.get(3),
            "config": dict(workload_desc(wl), sched=args.sched, launch=tuned), "launch": tuned}
@@ -490,7 +501,8 @@ def run_ours(args, rank, world, wl=None, full=True):
     peak_src = "measured" if os.path.exists(MEASURED) else "fallback"
     hbm_achieved = BYTES_PER_PARTICLE * nparts / (ms_part / 1e3) / 1e9
     hbm_obj = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
-               "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE}
+               "peak_source": peak_src, "bytes_per_particle": BYTES_PER_PARTICLE,
+               "frac_of_nominal": hbm_achieved / HBM_NOMINAL_GBS}
     kname = "pic_particle_kernel<%d,%d> (gather+Boris+Esirkepov+cost)" % (wl["dim"], wl["order"])
     if args.precision == 1:
         # the FP64 kernel is bound by the FP64 pipe: algorithmic flops against
@@ -561,7 +573,7 @@ def run_c3(args, steps=10):
         sim.rebalance(**dict(kw, theta=0.0))
         sim.set_lb_params(**kw)
         if tuned is None:
-            tuned = sim.autotune(steps_per_candidate=1)
+            tuned = sim.autotune(steps_per_candidate=2)
         else:
             sim.set_launch(**tuned)
         sim.step(2)
@@ -841,8 +853,8 @@ def main():
         torch.cuda.empty_cache()
         sec = run_ours(args, 0, 1, wl=make_workload(args.secondary, args.scale), full=False)
         sec = {"workload": sec["config"], "value": sec["value"], "unit": "particle-updates/s",
-               "ms_per_step": sec["ms_per_step"], "phase_ms_per_step": sec["phase_ms_per_step"],
-               "static_order": sec["static_order"], "mixed_precision": sec["mixed_precision"],
+               "ms_per_step": sec["ms_per_step"], "step_time_spread": sec["step_time_spread"],
+               "phase_ms_per_step": sec["phase_ms_per_step"], "static_order": sec["static_order"], "mixed_precision": sec["mixed_precision"],
                "fp32": sec["fp32"], "fdtd_cell_updates_per_s": sec["fdtd_cell_updates_per_s"],
                "hbm_frac_fp64": BYTES_PER_PARTICLE * sec["_nparts"]
                / (sec["phase_ms_per_step"]["particle"] / 1e3) / 1e9 / hbm_peak_gbs()}
@@ -858,7 +870,8 @@ def main():
     if rank == 0:
         line = {"metric": "particle-updates/s", "value": res["value"], "unit": "particle-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": res["ms_per_step"], "step_time_spread": res["step_time_spread"],
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {1: "f64", 2: "float-float", 3: "f32"}[args.precision],
                 "data": "synthetic (seeded PCG64 workload recipe)", "config": res["config"],
                 "clocks": res["clocks"], "e2e": res.get("e2e"),

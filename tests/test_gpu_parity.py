@@ -291,14 +291,19 @@ def test_autotune_searches_tile_and_particles_per_thread():
 
 
 @pytest.mark.parametrize("threads,cps", [(128, 1), (256, 2)])
-def test_launch_configuration_does_not_change_physics(threads, cps):
-    wl = workloads.random_plasma(78, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), 2, nspecies=1,
+@pytest.mark.parametrize("order,precision", [(2, 1), (1, 1), (1, 2), (1, 3)],
+                         ids=["o2_fp64", "o1_fp64", "o1_float_float", "o1_fp32"])
+def test_launch_configuration_does_not_change_physics(threads, cps, order, precision):
+    """Threads per CTA and the register budget change the per-thread work of
+    every staging pass (the x differences, the in-place conversions, the
+    particle staging buffers), not the physics."""
+    wl = workloads.random_plasma(78, 3, (16, 16, 16), (8, 8, 8), (0.3, 0.3, 0.3), order, nspecies=1,
                                  npart=5000, umax=1.0)
     sim, ref = make_gpu(wl), make_oracle(wl)
-    sim.set_launch(threads=threads, ctas_per_sm=cps)
+    sim.set_launch(threads=threads, ctas_per_sm=cps, precision=precision)
     sim.step(6)
     ref.step(6)
-    compare(sim, ref, wl)
+    compare(sim, ref, wl, tol=TOL if precision != 3 else TOL_FP32)
 
 
 def test_box_counts_and_clock_costs():

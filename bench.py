@@ -61,7 +61,7 @@ TRAFFIC_CAPTURE = {"bytes_per_particle": (501.010432e6 + 409.757440e6) / 8388608
                                "paper_2104_11385_gb300/csrc/pic_dd.cuh",
                                "paper_2104_11385_gb300/csrc/pic_internal.h",
                                "paper_2104_11385_gb300/csrc/pic_sync.cuh"),
-                   "sha256": "b7be8a1a47e4129732e72148b93f3b15890e5eec9a8e4e277e1e2d2d6e4fff71"}
+                   "sha256": "82cc630c91293752a1621f91ff9feac441b0448dc4fe5d75df8e4a03b78108c0"}
 
 
 def _kernel_sources_sha(paths):

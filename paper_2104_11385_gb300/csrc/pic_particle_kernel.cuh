@@ -423,8 +423,6 @@ __device__ __forceinline__ void tile_origin(const SimDev& S, int t, int o[3]) {
     o[2] = bz * S.bsz[2] + tz * S.T[2];
 }
 
-__device__ __forceinline__ int modi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
-
 // tile key of a global cell (box-major numbering); SV: SimDev or HotSim
 template <class SV>
 __device__ __forceinline__ int tile_key(const SV& S, int ix, int iy, int iz) {

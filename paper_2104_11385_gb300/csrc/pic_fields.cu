@@ -134,53 +134,60 @@ __global__ void damp_kernel(const SimDev* __restrict__ sims, const int* __restri
     }
 }
 
+// Visits the guard cells of the padded arrays, one warp per padded row (b, e):
+// the whole row when it lies in a y or z guard layer, else only the x guards
+// at its two ends (at most 8 cells).  f(c, i, j, k) gets the padded index and
+// the interior coordinates of the cell (outside [0, n) along some axis).  The
+// guards are a few per cent of the padded volume, and no thread divides
+// anything but its row index.
+template <class F>
+__device__ __forceinline__ void for_guard_cells(const SimDev& S, F&& f) {
+    const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int gl = S.g[0], gx = px - S.n[0];  // left x guards, both x guards
+    const int64_t rows = (int64_t)py * pz;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const int e = (int)(r / py), b = (int)(r - (int64_t)e * py);
+        const int j = b - S.g[1], k = e - S.g[2];
+        const int64_t row0 = r * px;
+        if (j < 0 || j >= S.n[1] || k < 0 || k >= S.n[2]) {
+            for (int a = lane; a < px; a += 32) f(row0 + a, a - gl, j, k);
+        } else if (lane < gx) {
+            const int a = lane < gl ? lane : S.n[0] + lane;
+            f(row0 + a, a - gl, j, k);
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap_cell(int i, int n) {
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
 // Current deposited in the guard cells of the padded J arrays (the particle
 // kernel's reductions reach up to 2 cells below and 3 above the domain) added
 // to its periodic image inside the domain.  Several guard cells share an image
-// (edges, corners), hence the reductions.  Guards of the FP32 variant, whose
-// tile flush wraps indices itself, hold zeros and are skipped.
+// (edges, corners), hence the reductions; guard cells holding zero are skipped.
 __global__ void fold_j_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
     const SimDev& S = slot_sim(sims, slots);
-    const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
-    const int64_t pvol = (int64_t)px * py * pz;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pvol;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int a = (int)(c % px);
-        int b = (int)((c / px) % py);
-        int e = (int)(c / ((int64_t)px * py));
-        int i = a - S.g[0], j = b - S.g[1], k = e - S.g[2];
-        bool inside = (i >= 0 && i < S.n[0]) && (j >= 0 && j < S.n[1]) && (k >= 0 && k < S.n[2]);
-        if (inside) continue;
-        const int64_t dst = pidx(S, ((i % S.n[0]) + S.n[0]) % S.n[0], ((j % S.n[1]) + S.n[1]) % S.n[1],
-                                 ((k % S.n[2]) + S.n[2]) % S.n[2]);
+    for_guard_cells(S, [&](int64_t c, int i, int j, int k) {
+        const int64_t dst = pidx(S, wrap_cell(i, S.n[0]), wrap_cell(j, S.n[1]), wrap_cell(k, S.n[2]));
 #pragma unroll
         for (int comp = 6; comp < 9; ++comp) {
             const double v = S.F[comp][c];
             if (v != 0.0) atomicAdd(S.F[comp] + dst, v);
         }
-    }
+    });
 }
 
 // periodic images into the guard cells of components [c0, c0+nc)
 __global__ void guard_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots, int c0,
                              int nc) {
     const SimDev& S = slot_sim(sims, slots);
-    const int px = S.pn[0], py = S.pn[1], pz = S.pn[2];
-    const int64_t pvol = (int64_t)px * py * pz;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pvol;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int a = (int)(c % px);
-        int b = (int)((c / px) % py);
-        int e = (int)(c / ((int64_t)px * py));
-        int i = a - S.g[0], j = b - S.g[1], k = e - S.g[2];
-        bool inside = (i >= 0 && i < S.n[0]) && (j >= 0 && j < S.n[1]) && (k >= 0 && k < S.n[2]);
-        if (inside) continue;
-        int si = ((i % S.n[0]) + S.n[0]) % S.n[0];
-        int sj = ((j % S.n[1]) + S.n[1]) % S.n[1];
-        int sk = ((k % S.n[2]) + S.n[2]) % S.n[2];
-        int64_t src = pidx(S, si, sj, sk);
+    for_guard_cells(S, [&](int64_t c, int i, int j, int k) {
+        const int64_t src = pidx(S, wrap_cell(i, S.n[0]), wrap_cell(j, S.n[1]), wrap_cell(k, S.n[2]));
         for (int comp = c0; comp < c0 + nc; ++comp) S.F[comp][c] = S.F[comp][src];
-    }
+    });
 }
 
 __global__ void unpad_kernel(const double* __restrict__ src, double* __restrict__ dst, SimDev S) {
@@ -271,6 +278,9 @@ __global__ void fill_kernel(double* p, int64_t n, double v) {
         p[i] = v;
 }
 
+// padded rows (y, z) of a simulation: one warp each in the guard kernels
+int64_t guard_rows(const SimDev& h) { return (int64_t)h.pn[1] * h.pn[2]; }
+
 int blocks_for(int64_t n, int t) {
     int64_t b = (n + t - 1) / t;
     if (b < 1) b = 1;
@@ -283,8 +293,7 @@ int blocks_for(int64_t n, int t) {
 cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t st) {
     const int64_t ncell = (int64_t)h.n[0] * h.n[1] * h.n[2];
     const int nb = blocks_for(ncell, 256);
-    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
-    fold_j_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr);
+    fold_j_kernel<<<blocks_for(guard_rows(h) * 32, 256), 256, 0, st>>>(dsim, nullptr);
     if (h.dim == 3) {
         b_half_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
         e_kernel<3><<<nb, 256, 0, st>>>(dsim, nullptr);
@@ -302,8 +311,7 @@ cudaError_t pic_launch_fields(const SimDev* dsim, const SimDev& h, cudaStream_t 
 }
 
 cudaError_t pic_launch_fold(const SimDev* dsim, const SimDev& h, cudaStream_t st) {
-    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
-    fold_j_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr);
+    fold_j_kernel<<<blocks_for(guard_rows(h) * 32, 256), 256, 0, st>>>(dsim, nullptr);
     return cudaGetLastError();
 }
 
@@ -328,8 +336,7 @@ cudaError_t pic_launch_field_stage(const SimDev* dsim, const SimDev& h, int stag
 
 cudaError_t pic_launch_guards(const SimDev* dsim, const SimDev& h, int c0, int nc,
                               cudaStream_t st) {
-    const int64_t pvol = (int64_t)h.pn[0] * h.pn[1] * h.pn[2];
-    guard_kernel<<<blocks_for(pvol, 256), 256, 0, st>>>(dsim, nullptr, c0, nc);
+    guard_kernel<<<blocks_for(guard_rows(h) * 32, 256), 256, 0, st>>>(dsim, nullptr, c0, nc);
     return cudaGetLastError();
 }
 

@@ -7,8 +7,8 @@
 // Each cell update reads E,B,J and writes E,B (120 bytes) with 39 FP64
 // operations (the time step over the cell size folded into the differences:
 // 12 per B half step, 15 for E): on GB300, whose FP64 rate is 1/64 of FP32,
-// that is FP64-bound, not HBM-bound.  One thread per cell, x fastest for
-// coalescing.
+// that is FP64-bound, not HBM-bound.  One warp per x row of cells, lanes
+// along x for coalescing; the guard kernels visit only the guard cells.
 #include "pic_internal.h"
 
 namespace {
@@ -21,11 +21,34 @@ __device__ __forceinline__ const SimDev& slot_sim(const SimDev* sims, const int*
     return sims[slots ? slots[blockIdx.y] : 0];
 }
 
+// Visits the interior cells this simulation owns, one warp per x row (j, k),
+// lanes along x (coalesced): f(i, j, k, o, oi, oj, ok) gets the cell's padded
+// index o and those of its periodic neighbours along x, y and z, the next ones
+// (FWD) or the previous ones.  Only the row index is divided.
+template <int DIM, bool FWD, class F>
+__device__ __forceinline__ void for_cells_by_row(const SimDev& S, F&& f) {
+    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+    const bool all_owned = S.owner == nullptr;
+    const int wpb = blockDim.x >> 5;
+    const int64_t rows = (int64_t)ny * nz;
+    auto nb = [](int i, int n) { return FWD ? nxt(i, n) : prv(i, n); };
+    for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const int k = (int)(r / ny), j = (int)(r - (int64_t)k * ny);
+        const int64_t row = pidx(S, 0, j, k);
+        const int64_t dj = (DIM == 3) ? pidx(S, 0, nb(j, ny), k) - row : 0;
+        const int64_t dk = pidx(S, 0, j, nb(k, nz)) - row;
+#pragma unroll 1
+        for (int i = threadIdx.x & 31; i < nx; i += 32) {
+            if (!all_owned && !cell_owned(S, i, j, k)) continue;
+            const int64_t o = row + i;
+            f(i, j, k, o, row + nb(i, nx), o + dj, o + dk);
+        }
+    }
+}
+
 template <int DIM>
 __global__ void b_half_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
     const SimDev& S = slot_sim(sims, slots);
-    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-    const int64_t ncell = (int64_t)nx * ny * nz;
     // B -= (dt/2) curl E with dt/(2 dx) folded into the differences: two FMAs
     // per component
     const double h = 0.5 * S.dt;
@@ -36,28 +59,27 @@ __global__ void b_half_kernel(const SimDev* __restrict__ sims, const int* __rest
     double* __restrict__ Bx = S.F[3];
     double* __restrict__ By = S.F[4];
     double* __restrict__ Bz = S.F[5];
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(c % nx);
-        int j = (int)((c / nx) % ny);
-        int k = (int)(c / ((int64_t)nx * ny));
-        if (!cell_owned(S, i, j, k)) continue;
-        int64_t o = pidx(S, i, j, k);
-        int64_t oi = pidx(S, nxt(i, nx), j, k);
-        int64_t oj = (DIM == 3) ? pidx(S, i, nxt(j, ny), k) : o;
-        int64_t ok = pidx(S, i, j, nxt(k, nz));
+    for_cells_by_row<DIM, true>(S, [&](int, int, int, int64_t o, int64_t oi, int64_t oj, int64_t ok) {
         const double ez = Ez[o], ey = Ey[o], ex = Ex[o];
         Bx[o] = fma(Ey[ok] - ey, hz, fma(-(Ez[oj] - ez), hy, Bx[o]));
         By[o] = fma(Ez[oi] - ez, hx, fma(-(Ex[ok] - ex), hz, By[o]));
         Bz[o] = fma(Ex[oj] - ex, hy, fma(-(Ey[oi] - ey), hx, Bz[o]));
-    }
+    });
+}
+
+// the antenna sheet's current at cell (i, j) of its layer (out of line: the
+// exp would otherwise raise the register count of every cell's update)
+template <int DIM>
+__device__ __noinline__ double antenna_jx(const SimDev& S, double amp, int i, int j) {
+    const LaserDev& L = S.las;
+    const double x = ((double)i + 0.5) * S.d[0] - L.xc;
+    const double y = (DIM == 3) ? (double)j * S.d[1] - L.yc : 0.0;
+    return amp * exp(-(x * x + y * y) / (L.w0 * L.w0));
 }
 
 template <int DIM>
 __global__ void e_kernel(const SimDev* __restrict__ sims, const int* __restrict__ slots) {
     const SimDev& S = slot_sim(sims, slots);
-    const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-    const int64_t ncell = (int64_t)nx * ny * nz;
     // E += dt (curl B - J) with dt/dx folded into the differences: three FMAs
     // per component
     const double dt = S.dt;
@@ -86,28 +108,17 @@ __global__ void e_kernel(const SimDev* __restrict__ sims, const int* __restrict_
     }
     __syncthreads();
     const double amp = s_amp;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(c % nx);
-        int j = (int)((c / nx) % ny);
-        int k = (int)(c / ((int64_t)nx * ny));
-        if (!cell_owned(S, i, j, k)) continue;
-        int64_t o = pidx(S, i, j, k);
-        int64_t oi = pidx(S, prv(i, nx), j, k);
-        int64_t oj = (DIM == 3) ? pidx(S, i, prv(j, ny), k) : o;
-        int64_t ok = pidx(S, i, j, prv(k, nz));
+    for_cells_by_row<DIM, false>(S, [&](int i, int j, int k, int64_t o, int64_t oi, int64_t oj, int64_t ok) {
         const double bx = Bx[o], by = By[o], bz = Bz[o];
         double jx = Jx[o];
         if (L.on && k == L.k_ant) {
-            double x = ((double)i + 0.5) * S.d[0] - L.xc;
-            double y = (DIM == 3) ? (double)j * S.d[1] - L.yc : 0.0;
-            jx += amp * exp(-(x * x + y * y) / (L.w0 * L.w0));
+            jx += antenna_jx<DIM>(S, amp, i, j);
             const_cast<double*>(Jx)[o] = jx;  // the antenna sheet is part of J^{n+1/2}
         }
         Ex[o] = fma(-dt, jx, fma(bz - Bz[oj], ty, fma(-(by - By[ok]), tz, Ex[o])));
         Ey[o] = fma(-dt, Jy[o], fma(bx - Bx[ok], tz, fma(-(bz - Bz[oi]), tx, Ey[o])));
         Ez[o] = fma(-dt, Jz[o], fma(by - By[oi], tx, fma(-(bx - Bx[oj]), ty, Ez[o])));
-    }
+    });
 }
 
 // E and B of cell layer k scaled by 1 - 0.5 (p/A)^2, p = depth inside the layer

@@ -157,6 +157,24 @@ def test_lognormal_uneven_boxes_parity_with_balancing():
     assert any(r["adopted"] for r in log)
 
 
+def test_heuristic_mapping_before_the_first_step():
+    """The heuristic cost needs only the particle counts, so a mapping can be
+    built from it before any step (a balanced start): it is adopted, cuts the
+    heavy boxes into work units, and the run stays on the oracle's trajectory
+    through it and the clock-cost mapping that follows."""
+    wl = workloads.lognormal(seed=7, nbox=(4, 4, 4), box=8, median=1500.0, sigma=1.5, order=1)
+    sim, ref = make_gpu(wl), make_oracle(wl)
+    lb = dict(mode=pic.LB_DYNAMIC, interval=3, policy=pic.POLICY_KNAPSACK, split=8)
+    r = sim.rebalance(**lb, theta=0.0, cost=pic.COST_HEURISTIC)
+    assert r["adopted"] and r["step"] == 0 and r["n_units"] > 64
+    assert r["e_new"] > r["e_old"]
+    sim.set_lb_params(**lb, theta=0.0, cost=pic.COST_DEVICE_CLOCK)
+    sim.step(7)
+    ref.step(7)
+    compare(sim, ref, wl)
+    assert [x["step"] for x in sim.lb_log()] == [0, 3, 6]
+
+
 def test_efficiency_of_the_mapping_in_force():
     """pic_get_efficiency reads the same cost window and mapping as the next
     load-balancing call (its E_old), and a reset leaves an empty window

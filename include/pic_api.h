@@ -230,7 +230,9 @@ pic_status pic_get_box_costs(pic_sim* sim, int strategy, double* costs_out, int6
  * (mode NONE is treated as DYNAMIC for an explicit call) and fills *out
  * (nullable).  assign_out: host, nboxes int32 (nullable) receives the worker
  * of each box's first unit under the mapping in force after the call.
- * Resets the accumulated device-clock costs.  Synchronises the stream. */
+ * With cost HEURISTIC the call needs only the particle counts, so it may run
+ * before the first step (a balanced start).  Resets the accumulated
+ * device-clock costs.  Synchronises the stream. */
 pic_status pic_rebalance(pic_sim* sim, const pic_lb_params* params, pic_lb_result* out,
                          int32_t* assign_out);
 

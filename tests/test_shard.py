@@ -1,5 +1,5 @@
 """Box sharding across ranks on the CPU (no GPU): the ghost-cell plans of
-libpic against brute force, and two gloo ranks running the orchestrator of
+libpic against brute force, and two or three gloo ranks running the orchestrator of
 paper_2104_11385_gb300.shard -- J ghost sum, E/B ghost exchange, particle
 migration and the cross-rank load-balancing routine with redistribution --
 over torch.distributed, with a numpy model of a rank in place of the GPU
@@ -169,18 +169,25 @@ class HostRank:
         return np.where(self.owner == self.rank, c, 0.0)
 
 
-def _setup(seed=5):
+OWNERS = {2: [0, 1, 1, 0, 1, 0, 0, 1, 1, 1, 0, 0],
+          3: [0, 1, 2, 2, 0, 1, 1, 2, 0, 0, 1, 2]}  # three ranks: every box borders the other two
+
+
+def _setup(seed=5, world=2):
     wl = {"dim": 3, "ncell": (16, 16, 24), "box": (8, 8, 8), "dx": (1.0, 1.0, 1.0), "species": [{}]}
     n = wl["ncell"]
     ncell = n[0] * n[1] * n[2]
     nboxes = 2 * 2 * 3
     rng = np.random.default_rng(seed)
-    owner = np.array([0, 1, 1, 0, 1, 0, 0, 1, 1, 1, 0, 0], np.int32)
+    owner = np.array(OWNERS[world], np.int32)
     # global fields; per-rank J contributions that live within 3 cells of the rank's boxes
     E = rng.normal(size=(6, ncell))
-    J = [np.zeros((3, ncell)) for _ in range(2)]
-    for r in range(2):
-        reach = np.union1d(_brute_halo(n, wl["box"], owner, r, r, 0, 3), _brute_halo(n, wl["box"], owner, 1 - r, r, 3, 3))
+    J = [np.zeros((3, ncell)) for _ in range(world)]
+    for r in range(world):
+        reach = _brute_halo(n, wl["box"], owner, r, r, 0, 3)
+        for o in range(world):
+            if o != r:
+                reach = np.union1d(reach, _brute_halo(n, wl["box"], owner, o, r, 3, 3))
         J[r][:, reach] = rng.normal(size=(3, reach.size))
     npart = 3000
     P = {"X": rng.uniform(0, n[0], npart), "Y": rng.uniform(0, n[1], npart), "Z": rng.uniform(0, n[2], npart),
@@ -194,23 +201,26 @@ def _rank_main(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        wl, owner, E, J, P, nboxes = _setup()
+        wl, owner, E, J, P, nboxes = _setup(world=world)
         n = wl["ncell"]
         cb = _cell_boxes(n, wl["box"])
         F = np.full((9, E.shape[1]), np.nan)
         mine = owner[cb] == rank
         F[:6, mine] = E[:, mine]                    # E/B valid on own boxes only
         F[6:9] = J[rank]                            # this rank's current contributions
-        parts = [{k: v[P["id"] % 2 == rank] for k, v in P.items()}]   # particles in the wrong place too
+        parts = [{k: v[P["id"] % world == rank] for k, v in P.items()}]   # particles in the wrong place too
         rk = HostRank(wl, rank, owner, F, parts)
         sim = SH.ShardedSimulation(wl, [rk], owner, world, SH.DistTransport("cpu"))
         res = {}
         # J ghost sum: own cells hold every rank's contribution
         sim._fields(6, 3, "J", True)
-        res["j_sum"] = bool(np.array_equal(rk.F[6:9, mine], (J[0] + J[1])[:, mine]))
+        res["j_sum"] = bool(np.allclose(rk.F[6:9, mine], sum(J)[:, mine], rtol=0, atol=1e-12))
         # E/B ghosts: own cells and every cell within 3 of own boxes hold the global values
         sim._fields(0, 6, "EB", False)
-        near = np.union1d(np.nonzero(mine)[0], _brute_halo(n, wl["box"], owner, 1 - rank, rank, 3, 3))
+        near = np.nonzero(mine)[0]
+        for o in range(world):
+            if o != rank:
+                near = np.union1d(near, _brute_halo(n, wl["box"], owner, o, rank, 3, 3))
         res["eb_ghosts"] = bool(np.array_equal(rk.F[:6, near], E[:, near]))
         # migration: every particle ends on the owner of its box, values intact
         sim._migrate()
@@ -241,28 +251,31 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def test_two_gloo_ranks_exchange_migrate_and_rebalance():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_exchange_migrate_and_rebalance(world):
+    """world ranks as gloo processes: the J ghost sum, the E/B ghost exchange,
+    migration and the cross-rank load-balancing routine (three ranks: every
+    box borders both other ranks)."""
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(300)
         assert p.exitcode == 0
-    r0, r1 = out[0], out[1]
-    for r in (r0, r1):
+    res = [out[r] for r in range(world)]
+    for r in res:
         assert r["j_sum"] and r["eb_ghosts"] and r["migrated_ok"] and r["values_ok"]
         assert r["moved_fields_ok"] and r["migrated2_ok"]
-    ids = sorted(r0["ids"] + r1["ids"])
-    assert ids == list(range(3000))
-    assert sorted(r0["ids2"] + r1["ids2"]) == list(range(3000))
-    # both ranks computed the same mapping and the same efficiencies
-    assert r0["owner"] == r1["owner"] and r0["rec"] == r1["rec"]
-    wl, owner, E, J, P, nboxes = _setup()
+    assert sorted(sum((r["ids"] for r in res), [])) == list(range(3000))
+    assert sorted(sum((r["ids2"] for r in res), [])) == list(range(3000))
+    # every rank computed the same mapping and the same efficiencies
+    assert all(r["owner"] == res[0]["owner"] and r["rec"] == res[0]["rec"] for r in res)
+    wl, owner, E, J, P, nboxes = _setup(world=world)
     counts = np.bincount(SH.box_of_positions({"dim": 3, "ncell": wl["ncell"], "box": wl["box"], "dx": (1, 1, 1)},
                                              P["X"], P["Y"], P["Z"]), minlength=nboxes).astype(float)
-    assert r0["rec"]["e_old"] == pytest.approx(SH.lb_efficiency(counts, owner, 2))
-    assert r0["rec"]["adopted"] == (r0["rec"]["e_new"] >= r0["rec"]["e_old"])
+    assert res[0]["rec"]["e_old"] == pytest.approx(SH.lb_efficiency(counts, owner, world))
+    assert res[0]["rec"]["adopted"] == (res[0]["rec"]["e_new"] >= res[0]["rec"]["e_old"])
